@@ -1,0 +1,268 @@
+/*
+ * pgm.h -- C ABI of libpgm: exact k-clique and k-motif counting on one
+ * NVIDIA B300 (sm_103a) with Pangolin's extend-reduce model.
+ *
+ * The calls follow the paper's statement of the problem (Sec. 2.1): given
+ * an input graph G and a pattern (a k-clique, or every connected k-vertex
+ * pattern for motif counting), return its support, which for these
+ * applications is the number of embeddings (Sec. 3.3, Listings 3-4).  The
+ * input is a simple undirected graph in CSR form with sorted neighbour
+ * lists (Sec. 6.1).
+ *
+ * Conventions shared by every call:
+ *   - Every call returns a pgm_status; no C++ exception crosses the ABI.
+ *   - Output arguments are written only when the call returns PGM_OK.
+ *   - Host buffers belong to the caller; the library copies what it needs.
+ *     Device memory allocated by the library belongs to the library and is
+ *     released by the matching destroy call.  "_dev" entry points read
+ *     caller-owned device buffers and never free them.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Calls that return counts synchronise that stream before
+ *     returning.
+ *   - A graph handle is immutable once oriented; counting calls on
+ *     different handles may run concurrently on different streams.  Calls
+ *     on the same handle must not overlap (they share its workspace).
+ *   - pgm_last_error() returns a thread-local message for the last failure.
+ *   - There is no CPU fallback: without a usable CUDA device every
+ *     counting call fails with PGM_ECUDA.
+ */
+#ifndef PGM_H
+#define PGM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  PGM_OK = 0,
+  PGM_EINVAL = -1,       /* malformed argument or input graph             */
+  PGM_EUNSUPPORTED = -2, /* k or size outside what this build supports    */
+  PGM_ENOMEM = -3,       /* device allocation failed or budget too small  */
+  PGM_ECUDA = -4,        /* CUDA runtime error (message in last_error)    */
+  PGM_ETIMEOUT = -5,     /* a bounded wait ran out                        */
+  PGM_EOVERFLOW = -6,    /* a count does not fit in uint64                */
+  PGM_EBUSY = -7         /* resource in use (server queue full, ...)      */
+} pgm_status;
+
+/* flags of pgm_graph_create_csr */
+#define PGM_VALIDATE 1u /* reject loops, duplicates, unsorted or asymmetric lists */
+#define PGM_SANITIZE 2u /* drop loops and duplicates, sort, symmetrise (host side) */
+
+typedef struct pgm_graph pgm_graph;   /* opaque: device CSR + oriented DAG */
+typedef struct pgm_batch pgm_batch;   /* opaque: disjoint union of many graphs */
+typedef struct pgm_server pgm_server; /* opaque: request loop over resident graphs */
+
+/* Summary of a graph (exact integers). */
+typedef struct {
+  int64_t n;            /* vertices                                  */
+  int64_t m;            /* undirected edges                          */
+  int64_t dmax;         /* maximum degree                            */
+  int64_t dag_dmax;     /* maximum out-degree of the oriented DAG (0 before orientation) */
+  uint64_t sum_c2[2];   /* sum_v C(d_v, 2) as a 128-bit value (low, high) */
+  uint64_t sum_c3[2];   /* sum_v C(d_v, 3) as a 128-bit value (low, high) */
+} pgm_graph_stats;
+
+/* Tunables (pgm_set_options / pgm_get_options).  Zero keeps the current value. */
+typedef struct {
+  int32_t block_threads;   /* threads per block of the warp-per-parent kernels, 64..512 (default 256) */
+  int32_t warp_stage_cap;  /* per-warp shared-memory staging capacity, ints (default 512)     */
+  int32_t hub_threshold;   /* segment length that moves a parent to the block-per-parent kernel (default = warp_stage_cap) */
+  int32_t blocks_per_sm;   /* persistent-grid blocks per SM (default 0 = occupancy-derived)   */
+  int64_t level_budget;    /* max entries of one materialised level chunk (edge blocking, default 1<<29) */
+  int32_t profile;         /* 1 = record per-launch CUDA-event times (pgm_last_profile)       */
+  int32_t reserved[7];
+} pgm_options;
+
+/* Per-call profile (when options.profile = 1): one record per kernel phase. */
+#define PGM_PROFILE_MAX 64
+typedef struct {
+  char name[32];          /* kernel / phase name                                   */
+  int32_t level;          /* embedding level the phase works on                    */
+  int32_t launches;       /* launches merged into this record                      */
+  double ms;              /* summed CUDA-event time of those launches              */
+  double entries;         /* embeddings read by the phase                          */
+  double alg_bytes;       /* algorithmic bytes (adjacency lists + records) moved   */
+} pgm_phase;
+
+typedef struct {
+  int32_t nphases;
+  pgm_phase phase[PGM_PROFILE_MAX];
+  uint64_t level_size[16]; /* |L_l| for l = 1..k (index l) of the last count call */
+  int32_t chunks;          /* edge-blocking chunks used                            */
+} pgm_profile;
+
+/* ---------------------------------------------------------------- graphs */
+
+/* Create a graph from a host CSR (Sec. 6.1 input format: symmetric, no
+ * self-loops, no duplicate edges, neighbour lists sorted ascending).
+ *   n       vertices, 0 <= n < 2^31
+ *   rowptr  host int64[n+1], rowptr[0] = 0, non-decreasing; total arcs
+ *           rowptr[n] < 2^31
+ *   col     host int32[rowptr[n]] neighbour IDs
+ *   flags   PGM_VALIDATE checks the format on the device and fails with
+ *           PGM_EINVAL on a violation; PGM_SANITIZE repairs it on the host
+ *           first (the two may be combined).  0 trusts the input.
+ *   stream  stream used for the upload and every later call on the handle
+ *   out     receives the handle (library-owned; free with pgm_graph_destroy)
+ * The host arrays are copied; the caller keeps ownership. */
+pgm_status pgm_graph_create_csr(int32_t n, const int64_t *rowptr, const int32_t *col,
+                                uint32_t flags, void *stream, pgm_graph **out);
+
+/* Same, from caller-owned DEVICE arrays (int64 rowptr, int32 col); the
+ * library copies them into its own buffers.  PGM_SANITIZE is not accepted. */
+pgm_status pgm_graph_create_csr_dev(int32_t n, const int64_t *rowptr_dev, const int32_t *col_dev,
+                                    int64_t narcs, uint32_t flags, void *stream, pgm_graph **out);
+
+/* Orient the graph into a DAG (Sec. 4.1, "Directed Acyclic Graph"): arc
+ * u->v is kept iff (d(u), u) < (d(v), v), i.e. edges point to the vertex of
+ * higher degree and ties to the larger ID.  Out-lists stay ID-sorted.
+ * Idempotent.  Needed by pgm_count_kcliques (called implicitly there). */
+pgm_status pgm_graph_orient_by_degree(pgm_graph *g);
+
+/* Exact summary statistics (degrees from the CSR). */
+pgm_status pgm_graph_stats_get(const pgm_graph *g, pgm_graph_stats *out);
+
+void pgm_graph_destroy(pgm_graph *g);
+
+/* --------------------------------------------------------------- counting */
+
+/* Number of k-cliques (Sec. 2.2; Sec. 3.3 Listing 3 "clique finding"):
+ * k-vertex subsets whose vertices are pairwise adjacent.  k = 1 gives n,
+ * k = 2 gives m; k in [3, 10] runs the level-wise engine on the oriented
+ * DAG: extension of the last vertex only (eager pruning, Sec. 4.1), a
+ * connectivity check of each candidate against the embedding by sorted
+ * intersection with the parent's candidate list, inspection-execution
+ * between materialised levels (Sec. 5.3), edge blocking (Sec. 5.2), and a
+ * fused count at the last level (Sec. 3.1, reduce only at the last level).
+ * Orients the graph first if needed.  Returns PGM_EUNSUPPORTED outside
+ * [1, 10]. */
+pgm_status pgm_count_kcliques(pgm_graph *g, int32_t k, uint64_t *out_count);
+
+/* The part of the k-clique count whose first DAG vertex lies in
+ * [v_lo, v_hi): the edge-blocking unit (Sec. 5.2) used to shard one count
+ * across devices or processes; the parts over a partition of [0, n) add up
+ * to pgm_count_kcliques. */
+pgm_status pgm_count_kcliques_range(pgm_graph *g, int32_t k, int32_t v_lo, int32_t v_hi,
+                                    uint64_t *out_count);
+
+/* Vertex-induced motif counts (Sec. 2.2; Sec. 3.3 Listing 4 "motif
+ * counting"; customised classification Sec. 4.2, Listing 6): for each
+ * connected k-vertex pattern, the number of vertex sets whose induced
+ * subgraph is that pattern, each set counted once (canonical test,
+ * Sec. 3.2).  Output order:
+ *   k = 3: [wedge, triangle]                                   (cap >= 2)
+ *   k = 4: [3-star, 4-path, tailed-triangle, 4-cycle, diamond, 4-clique] (cap >= 6)
+ * Other k: PGM_EUNSUPPORTED.  Requires n < 2^30. */
+pgm_status pgm_count_motifs(pgm_graph *g, int32_t k, uint64_t *out_counts, int32_t cap);
+
+/* Motif counts of the embeddings whose first vertex (the minimum ID)
+ * lies in [v_lo, v_hi); additive over a partition of [0, n). */
+pgm_status pgm_count_motifs_range(pgm_graph *g, int32_t k, int32_t v_lo, int32_t v_hi,
+                                  uint64_t *out_counts, int32_t cap);
+
+/* --------------------------------------------------------------- batches */
+
+/* A batch is the disjoint union of G graphs in one concatenated CSR: graph
+ * i owns the vertices [vtx_off[i], vtx_off[i+1]) and its arcs use those
+ * global IDs (no arc may leave its graph; PGM_EINVAL otherwise).  Host
+ * arrays:
+ *   vtx_off     int64[G+1], vtx_off[0] = 0, non-decreasing
+ *   rowptr_cat  int64[vtx_off[G]+1]
+ *   col_cat     int32[rowptr_cat[vtx_off[G]]]
+ * (not in the paper: many-small-graphs batching). */
+pgm_status pgm_batch_create(int32_t G, const int64_t *vtx_off, const int64_t *rowptr_cat,
+                            const int32_t *col_cat, uint32_t flags, void *stream, pgm_batch **out);
+
+/* Tunables of the batched path, chosen by pgm_batch_autotune or by hand.
+ * Zero fields keep the library defaults. */
+typedef struct {
+  int32_t block_threads;  /* threads per block, 64..512           */
+  int32_t warp_stage_cap; /* per-warp staging capacity (ints)     */
+  int32_t hub_threshold;  /* block-per-parent threshold           */
+  int32_t blocks_per_sm;  /* persistent grid size per SM          */
+  int32_t use_graph;      /* 1 = replay a captured CUDA graph     */
+  int32_t reserved[3];
+} pgm_tune;
+
+/* Per-graph motif counts of every graph of the batch in one pass of the
+ * level engine over the union (persistent kernels pulling parents from a
+ * device queue, counts attributed per graph), optionally replayed as a
+ * captured CUDA graph.  out: host uint64[G * (k==3 ? 2 : 6)], row i =
+ * graph i in pgm_count_motifs order.  t may be NULL (defaults). */
+pgm_status pgm_batch_count_motifs(pgm_batch *b, int32_t k, uint64_t *out, const pgm_tune *t);
+
+/* Per-graph k-clique counts (out: host uint64[G]). */
+pgm_status pgm_batch_count_kcliques(pgm_batch *b, int32_t k, uint64_t *out, const pgm_tune *t);
+
+/* The baseline the batched path is measured against: the same counts by
+ * one plain pgm_count_motifs-style launch sequence per graph, in a host
+ * loop on one stream (same device data, natural per-level syncs). */
+pgm_status pgm_batch_count_motifs_loop(pgm_batch *b, int32_t k, uint64_t *out);
+
+/* Time candidate pgm_tune settings on this batch and return the fastest
+ * (exact counts are identical for every setting; a mismatch is reported
+ * as PGM_EINVAL). */
+pgm_status pgm_batch_autotune(pgm_batch *b, int32_t k, pgm_tune *best, double *best_ms);
+
+int32_t pgm_batch_size(const pgm_batch *b);
+void pgm_batch_destroy(pgm_batch *b);
+
+/* ---------------------------------------------------------------- server */
+
+typedef enum { PGM_Q_TRIANGLE = 0, PGM_Q_KCLIQUE = 1, PGM_Q_MOTIF = 2 } pgm_query_kind;
+
+typedef struct {
+  int32_t kind;   /* pgm_query_kind                                   */
+  int32_t k;      /* clique size (KCLIQUE) or motif size (MOTIF)      */
+  int32_t graph;  /* resident graph id returned by pgm_server_add_graph */
+  int32_t pad;
+} pgm_query;
+
+typedef struct {
+  int32_t done;       /* 1 when the result is final                      */
+  int32_t status;     /* pgm_status of the query                          */
+  uint64_t counts[6]; /* clique count in [0], or motif counts             */
+  double submit_s;    /* host clock (s) at submission                     */
+  double start_s;     /* host clock when admitted to the device           */
+  double finish_s;    /* host clock when the result was seen on the host  */
+  int64_t mem_bytes;  /* predicted embedding-list bytes used for admission */
+} pgm_result;
+
+/* Request loop over device-resident graphs (not in the paper: serving).
+ * budget_bytes bounds the predicted embedding-list memory of the queries
+ * in flight; max_inflight bounds the concurrent queries (one CUDA stream
+ * and one workspace each).  Worker threads admit queued queries as memory
+ * and slots free up, so queries on different graphs overlap on the GPU. */
+pgm_status pgm_server_create(int64_t budget_bytes, int32_t max_inflight, pgm_server **out);
+/* Upload a graph (host CSR as in pgm_graph_create_csr) and orient it. */
+pgm_status pgm_server_add_graph(pgm_server *s, int32_t n, const int64_t *rowptr,
+                                const int32_t *col, int32_t *graph_id);
+/* Queue a query; *ticket identifies it in pgm_server_poll. */
+pgm_status pgm_server_submit(pgm_server *s, const pgm_query *q, int64_t *ticket);
+/* Non-blocking: copies the current state of the ticket's result. */
+pgm_status pgm_server_poll(pgm_server *s, int64_t ticket, pgm_result *out);
+/* Block until every submitted query is done (PGM_ETIMEOUT after timeout_s). */
+pgm_status pgm_server_drain(pgm_server *s, double timeout_s);
+void pgm_server_destroy(pgm_server *s);
+
+/* ---------------------------------------------------------------- misc */
+
+pgm_status pgm_set_options(const pgm_options *o);
+pgm_status pgm_get_options(pgm_options *o);
+/* Profile of the last counting call made by this thread (options.profile). */
+pgm_status pgm_last_profile(pgm_profile *out);
+/* Exclusive prefix sum on the device (inspection-execution's allocation
+ * step, Sec. 5.3): out[i] = sum of cnt[0..i-1], out[len] = total.  Device
+ * pointers: cnt uint32[len], out int64[len+1].  Synchronises the stream. */
+pgm_status pgm_exclusive_scan_dev(const uint32_t *cnt_dev, int64_t len, int64_t *out_dev,
+                                  void *stream);
+const char *pgm_last_error(void);
+const char *pgm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PGM_H */

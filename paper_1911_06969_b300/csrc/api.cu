@@ -1,0 +1,273 @@
+// api.cu -- process-wide state of libpgm: error messages, options, device
+// queries, the launch profiler, record/replay plans and the small C-ABI
+// entry points.
+#include <algorithm>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <utility>
+
+#include "common.cuh"
+
+namespace pgm {
+
+static thread_local std::string t_err;
+
+void set_error(const char* fmt, ...) {
+  char buf[1024];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  t_err = buf;
+}
+
+const char* get_error() { return t_err.c_str(); }
+
+static pgm_options g_opts = {256, 512, 0, 0, (int64_t)1 << 29, 0, {0}};
+
+pgm_options& options() { return g_opts; }
+
+int device_id() {
+  int d = 0;
+  cudaGetDevice(&d);
+  return d;
+}
+
+int num_sms() {
+  static int cached[64] = {0};
+  static std::mutex mu;
+  int d = device_id();
+  if (d < 0 || d >= 64) return 148;
+  std::lock_guard<std::mutex> lk(mu);
+  if (!cached[d]) {
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, d) != cudaSuccess || v <= 0) {
+      cudaGetLastError();
+      v = 148;
+    }
+    cached[d] = v;
+  }
+  return cached[d];
+}
+
+// occupancy is cached per (kernel, block size, shared memory) so that no
+// runtime query happens while a stream is being captured
+int grid_for(const void* fn, int threads, size_t smem) {
+  int per_sm = options().blocks_per_sm;
+  if (per_sm <= 0) {
+    static std::mutex mu;
+    static std::map<std::tuple<const void*, int, size_t>, int> cache;
+    std::lock_guard<std::mutex> lk(mu);
+    auto key = std::make_tuple(fn, threads, smem);
+    auto it = cache.find(key);
+    if (it != cache.end()) {
+      per_sm = it->second;
+    } else {
+      int occ = 0;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, threads, smem) != cudaSuccess ||
+          occ <= 0) {
+        cudaGetLastError();
+        occ = 1;
+      }
+      cache[key] = occ;
+      per_sm = occ;
+    }
+  }
+  return per_sm * num_sms();
+}
+
+pgm_status smem_attr(const void* fn, int bytes) {
+  static std::mutex mu;
+  static std::map<const void*, int> done;
+  std::lock_guard<std::mutex> lk(mu);
+  auto it = done.find(fn);
+  if (it != done.end() && it->second >= bytes) return PGM_OK;
+  PGM_TRY_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  done[fn] = bytes;
+  return PGM_OK;
+}
+
+// ---------------------------------------------------------------- profiler
+static thread_local Profiler t_prof;
+static thread_local pgm_profile t_last;
+static thread_local std::vector<cudaEvent_t> t_event_pool;
+
+Profiler& profiler() { return t_prof; }
+pgm_profile& last_profile() { return t_last; }
+
+static cudaEvent_t take_event() {
+  if (!t_event_pool.empty()) {
+    cudaEvent_t e = t_event_pool.back();
+    t_event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return e;
+}
+
+void Profiler::start(cudaStream_t s) {
+  for (auto& r : recs) {
+    if (r.a) t_event_pool.push_back(r.a);
+    if (r.b) t_event_pool.push_back(r.b);
+  }
+  recs.clear();
+  stream = s;
+  on = options().profile != 0;
+  memset(&t_last, 0, sizeof(t_last));
+}
+
+int Profiler::begin(const char* name, int level) {
+  if (!on) return -1;
+  Rec r;
+  r.name = name;
+  r.level = level;
+  r.a = take_event();
+  r.b = take_event();
+  r.entries = 0;
+  r.alg_bytes = 0;
+  if (!r.a || !r.b) return -1;
+  cudaEventRecord(r.a, stream);
+  recs.push_back(r);
+  return (int)recs.size() - 1;
+}
+
+void Profiler::end(int id, double entries, double alg_bytes) {
+  if (id < 0 || id >= (int)recs.size()) return;
+  cudaEventRecord(recs[id].b, stream);
+  recs[id].entries = entries;
+  recs[id].alg_bytes = alg_bytes;
+}
+
+pgm_status Profiler::finish(pgm_profile* out) {
+  if (!on) return PGM_OK;
+  PGM_TRY_CUDA(cudaStreamSynchronize(stream));
+  std::map<std::pair<std::string, int>, int> slot;
+  for (auto& r : recs) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, r.a, r.b) != cudaSuccess) {
+      cudaGetLastError();
+      ms = 0.f;
+    }
+    auto key = std::make_pair(r.name, r.level);
+    auto it = slot.find(key);
+    int i;
+    if (it == slot.end()) {
+      if (out->nphases >= PGM_PROFILE_MAX) continue;
+      i = out->nphases++;
+      slot[key] = i;
+      pgm_phase& p = out->phase[i];
+      memset(&p, 0, sizeof(p));
+      strncpy(p.name, r.name.c_str(), sizeof(p.name) - 1);
+      p.level = r.level;
+    } else {
+      i = it->second;
+    }
+    pgm_phase& p = out->phase[i];
+    p.launches += 1;
+    p.ms += ms;
+    p.entries += r.entries;
+    p.alg_bytes += r.alg_bytes;
+  }
+  return PGM_OK;
+}
+
+// ------------------------------------------------------------------ plans
+static thread_local Plan* t_plan = nullptr;
+Plan*& current_plan() { return t_plan; }
+
+pgm_status read_counters(const unsigned long long* dev, unsigned long long* host, size_t n,
+                         cudaStream_t s, bool* deferred) {
+  Plan* pl = current_plan();
+  if (pl && pl->replay && pl->pinned_ctr) {
+    PGM_TRY_CUDA(cudaMemcpyAsync(pl->pinned_ctr, dev, n * sizeof(unsigned long long),
+                                 cudaMemcpyDeviceToHost, s));
+    *deferred = true;
+    return PGM_OK;
+  }
+  PGM_TRY_CUDA(cudaMemcpyAsync(host, dev, n * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+  PGM_TRY_CUDA(cudaStreamSynchronize(s));
+  *deferred = false;
+  return PGM_OK;
+}
+
+void Workspace::release_all() {
+  for (int i = 0; i < kMaxLevels; i++) {
+    cnt[i].release();
+    off[i].release();
+    vid[i].release();
+  }
+  big.release();
+  ctr.release();
+  scan_tmp.release();
+  scratch.release();
+}
+
+}  // namespace pgm
+
+// ------------------------------------------------------------------- C ABI
+extern "C" {
+
+const char* pgm_last_error(void) { return pgm::get_error(); }
+
+const char* pgm_version(void) { return "libpgm 0.2 (sm_103a)"; }
+
+pgm_status pgm_set_options(const pgm_options* o) {
+  if (!o) {
+    pgm::set_error("pgm_set_options: null options");
+    return PGM_EINVAL;
+  }
+  pgm_options v = *o;
+  pgm_options& cur = pgm::options();
+  if (v.block_threads) {
+    if (v.block_threads < 64 || v.block_threads > 512 || v.block_threads % 32) {
+      pgm::set_error("block_threads must be a multiple of 32 in [64, 512]");
+      return PGM_EINVAL;
+    }
+    cur.block_threads = v.block_threads;
+  }
+  if (v.warp_stage_cap) {
+    if (v.warp_stage_cap < 32 || v.warp_stage_cap > 4096) {
+      pgm::set_error("warp_stage_cap must be in [32, 4096]");
+      return PGM_EINVAL;
+    }
+    cur.warp_stage_cap = v.warp_stage_cap;
+  }
+  if (v.hub_threshold) {
+    if (v.hub_threshold < 2) {
+      pgm::set_error("hub_threshold must be >= 2");
+      return PGM_EINVAL;
+    }
+    cur.hub_threshold = v.hub_threshold;
+  }
+  if (v.blocks_per_sm) cur.blocks_per_sm = v.blocks_per_sm < 0 ? 0 : v.blocks_per_sm;
+  if (v.level_budget) {
+    if (v.level_budget < 1024) {
+      pgm::set_error("level_budget must be >= 1024 entries");
+      return PGM_EINVAL;
+    }
+    cur.level_budget = v.level_budget;
+  }
+  cur.profile = v.profile ? 1 : 0;
+  return PGM_OK;
+}
+
+pgm_status pgm_get_options(pgm_options* o) {
+  if (!o) return PGM_EINVAL;
+  *o = pgm::options();
+  if (!o->hub_threshold) o->hub_threshold = o->warp_stage_cap;
+  return PGM_OK;
+}
+
+pgm_status pgm_last_profile(pgm_profile* out) {
+  if (!out) return PGM_EINVAL;
+  *out = pgm::last_profile();
+  return PGM_OK;
+}
+
+}  // extern "C"

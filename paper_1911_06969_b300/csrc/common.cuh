@@ -1,0 +1,249 @@
+// common.cuh -- internals shared by the libpgm translation units: error
+// reporting, options, device workspaces, launch profiling, record/replay
+// plans and the warp-level primitives of the level engine (sorted-list
+// search, warp scan).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdarg>
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "../../include/pgm.h"
+
+namespace pgm {
+
+// ------------------------------------------------------------------ errors
+void set_error(const char* fmt, ...);
+const char* get_error();
+
+#define PGM_TRY_CUDA(expr)                                                                     \
+  do {                                                                                         \
+    cudaError_t e_ = (expr);                                                                   \
+    if (e_ != cudaSuccess) {                                                                   \
+      ::pgm::set_error("%s failed: %s (%s:%d)", #expr, cudaGetErrorString(e_), __FILE__,      \
+                       __LINE__);                                                              \
+      return e_ == cudaErrorMemoryAllocation ? PGM_ENOMEM : PGM_ECUDA;                         \
+    }                                                                                          \
+  } while (0)
+
+#define PGM_TRY(expr)            \
+  do {                           \
+    pgm_status s_ = (expr);      \
+    if (s_ != PGM_OK) return s_; \
+  } while (0)
+
+#define PGM_CHECK_LAUNCH() PGM_TRY_CUDA(cudaGetLastError())
+
+// ----------------------------------------------------------------- options
+pgm_options& options();  // current options (defaults filled); read-only while counting
+int num_sms();            // SM count of the current device
+int device_id();
+
+// ------------------------------------------------------------ device array
+// Grow-only device buffer owned by a handle; never shrinks until freed.
+template <typename T>
+struct DevArr {
+  T* p = nullptr;
+  size_t cap = 0;  // elements
+  pgm_status reserve(size_t n) {
+    if (n <= cap && p) return PGM_OK;
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+    size_t want = n ? n : 1;
+    cudaError_t e = cudaMalloc(&p, want * sizeof(T));
+    if (e != cudaSuccess) {
+      p = nullptr;
+      cudaGetLastError();
+      set_error("cudaMalloc of %zu bytes failed: %s", want * sizeof(T), cudaGetErrorString(e));
+      return PGM_ENOMEM;
+    }
+    cap = want;
+    return PGM_OK;
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+  }
+};
+
+// --------------------------------------------------------------- profiling
+// Records CUDA events around each kernel launch on the launching stream
+// when options().profile is set; folded into pgm_phase rows at the end of
+// a public call.
+struct Profiler {
+  struct Rec {
+    std::string name;
+    int level;
+    cudaEvent_t a, b;
+    double entries, alg_bytes;
+  };
+  cudaStream_t stream = nullptr;
+  bool on = false;
+  std::vector<Rec> recs;
+  void start(cudaStream_t s);
+  int begin(const char* name, int level);             // returns record id or -1
+  void end(int id, double entries, double alg_bytes);  // after the launch
+  pgm_status finish(pgm_profile* out);                 // sync + fold into out
+};
+Profiler& profiler();         // thread-local
+pgm_profile& last_profile();  // thread-local result of the last call
+
+// ------------------------------------------------------------ graph state
+// Scratch of one counting call: level lists, counters, hub queues.  A graph
+// handle owns one; the server owns one per in-flight slot.
+struct Workspace {
+  static constexpr int kMaxLevels = 12;
+  DevArr<uint32_t> cnt[kMaxLevels];  // per-entry child counts (inspection)
+  DevArr<int64_t> off[kMaxLevels];   // exclusive scan of cnt (execution offsets)
+  DevArr<int32_t> vid[kMaxLevels];   // materialised level lists
+  DevArr<int64_t> big;               // hub parents of one launch
+  DevArr<unsigned long long> ctr;    // queue counters + accumulators
+  DevArr<int64_t> scan_tmp;          // block partials of the scan
+  DevArr<int32_t> scratch;           // per-warp spill lists of the hub kernels
+  void release_all();
+};
+
+// Device-resident graph.  Everything but `ws` is immutable after
+// orientation and motif preparation, so several streams may count on it
+// concurrently with their own workspaces.
+struct Graph {
+  int32_t n = 0;
+  int64_t narcs = 0;           // 2 m
+  int32_t* rp = nullptr;       // int32[n+1] undirected CSR
+  int32_t* col = nullptr;      // int32[narcs]
+  int32_t* dag_rp = nullptr;   // int32[n+1] oriented DAG
+  int32_t* dag_col = nullptr;  // int32[m]
+  int32_t* up = nullptr;       // up[v] = first arc of v whose neighbour is > v
+  int32_t* gid = nullptr;      // batches: vertex -> graph id (nullptr otherwise)
+  int32_t G = 1;
+  int64_t dmax = 0, dag_dmax = 0;
+  bool oriented = false;
+  cudaStream_t stream = nullptr;
+  std::vector<int64_t> h_dag_rp;  // host copy of the DAG row pointers (edge blocking)
+  std::vector<int64_t> h_rp;      // host copy of the CSR row pointers
+  Workspace ws;                   // workspace of calls made through the handle
+};
+
+pgm_status graph_upload(Graph& g, int32_t n, const int64_t* rowptr, const int32_t* col,
+                        bool rowptr_on_device, int64_t narcs, uint32_t flags, cudaStream_t s);
+pgm_status graph_orient(Graph& g);
+pgm_status graph_prepare_motifs(Graph& g);
+void graph_free(Graph& g);
+
+// scan: out[i] = sum cnt[0..i), out[len] = total (device pointers)
+pgm_status exclusive_scan(const uint32_t* cnt, int64_t len, int64_t* out, Workspace& ws,
+                          cudaStream_t s);
+
+// ------------------------------------------------------- record / replay
+// The engines read a few values back from the device (level totals and
+// edge-blocking boundaries).  A Plan recorded on a first run lets the same
+// launch sequence be replayed without those reads -- the condition for
+// capturing it in a CUDA graph.  In replay mode the final counter readback
+// is an async copy into `pinned_ctr`, read by the caller after the stream
+// (or graph launch) completes.
+struct Plan {
+  bool record = false;
+  bool replay = false;
+  std::vector<int64_t> v;
+  size_t cur = 0;
+  unsigned long long* pinned_ctr = nullptr;  // host-pinned copy target (replay)
+};
+Plan*& current_plan();  // thread-local, nullptr when not planning
+
+template <typename T>
+pgm_status read_dev(const T* p, T* out, cudaStream_t s) {
+  Plan* pl = current_plan();
+  if (pl && pl->replay) {
+    if (pl->cur >= pl->v.size()) {
+      set_error("plan replay: more reads than recorded");
+      return PGM_EINVAL;
+    }
+    *out = (T)pl->v[pl->cur++];
+    return PGM_OK;
+  }
+  PGM_TRY_CUDA(cudaMemcpyAsync(out, p, sizeof(T), cudaMemcpyDeviceToHost, s));
+  PGM_TRY_CUDA(cudaStreamSynchronize(s));
+  if (pl && pl->record) pl->v.push_back((int64_t)*out);
+  return PGM_OK;
+}
+
+// Final readback of an engine's counter block: synchronous normally, an
+// async copy into the plan's pinned buffer when replaying (then *deferred
+// is set and the values are not yet on the host).
+pgm_status read_counters(const unsigned long long* dev, unsigned long long* host, size_t n,
+                         cudaStream_t s, bool* deferred);
+
+// counting engines (results written on PGM_OK; per_graph_dev: batches)
+pgm_status count_kcliques(Graph& g, Workspace& ws, cudaStream_t s, int k, int32_t v_lo,
+                          int32_t v_hi, uint64_t* out, unsigned long long* per_graph_dev);
+pgm_status count_motifs(Graph& g, Workspace& ws, cudaStream_t s, int k, int32_t v_lo,
+                        int32_t v_hi, uint64_t* out, unsigned long long* per_graph_dev);
+
+// persistent-grid size for a kernel
+int grid_for(const void* fn, int threads, size_t smem);
+// raise a kernel's dynamic shared-memory limit once per process
+pgm_status smem_attr(const void* fn, int bytes);
+
+// -------------------------------------------------------- device helpers
+constexpr unsigned kFull = 0xffffffffu;
+
+// first index i in [0, n) with a[i] >= x (n if none)
+__device__ __forceinline__ int lower_bound_dev(const int32_t* __restrict__ a, int n, int32_t x) {
+  int lo = 0;
+  while (n > 0) {
+    int half = n >> 1;
+    int32_t v = a[lo + half];
+    if (v < x) {
+      lo += half + 1;
+      n -= half + 1;
+    } else {
+      n = half;
+    }
+  }
+  return lo;
+}
+
+__device__ __forceinline__ bool contains_dev(const int32_t* __restrict__ a, int n, int32_t x) {
+  int i = lower_bound_dev(a, n, x);
+  return i < n && a[i] == x;
+}
+
+__device__ __forceinline__ int warp_inclusive_scan(int v, int lane) {
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    int t = __shfl_up_sync(kFull, v, d);
+    if (lane >= d) v += t;
+  }
+  return v;
+}
+
+// lane of the owner of item t, given each lane's inclusive prefix `incl`
+// of item counts (non-decreasing): the number of incl values <= t
+__device__ __forceinline__ int warp_owner(int incl, int t) {
+  int q = 0;
+#pragma unroll
+  for (int step = 16; step > 0; step >>= 1) {
+    int v = __shfl_sync(kFull, incl, q + step - 1);
+    if (v <= t) q += step;
+  }
+  return q;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(kFull, v, d);
+  return v;
+}
+
+}  // namespace pgm
+
+struct pgm_graph {
+  pgm::Graph g;
+};

@@ -1,0 +1,379 @@
+// graph.cu -- CSR ingest, validation, degree orientation and statistics.
+//
+// Input format (Sec. 6.1): simple undirected graph, CSR with neighbour
+// lists sorted by ascending ID, symmetric, without self-loops or duplicate
+// edges.  On the device the graph is int32 row pointers + int32 columns.
+//
+// Orientation (Sec. 4.1, "Directed Acyclic Graph"): arc u->v is kept iff
+// (d(u), u) < (d(v), v) -- edges point to the higher degree, ties to the
+// larger ID.  Each vertex's out-list keeps the ID order of its undirected
+// list, so DAG lists stay sorted.
+#include <algorithm>
+#include <cstring>
+#include <new>
+
+#include "common.cuh"
+
+namespace pgm {
+
+enum : unsigned {
+  kBadRange = 1u,    // neighbour ID outside [0, n)
+  kUnsorted = 2u,    // list not strictly ascending (unsorted or duplicate)
+  kSelfLoop = 4u,
+  kAsymmetric = 8u,
+};
+
+// one warp per vertex: checks IDs, order, loops and symmetry
+__global__ void validate_kernel(int32_t n, const int32_t* __restrict__ rp,
+                                const int32_t* __restrict__ col, unsigned* __restrict__ flags) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  unsigned bad = 0;
+  for (int64_t u = warp; u < n; u += nwarps) {
+    const int32_t a0 = rp[u], a1 = rp[u + 1];
+    for (int32_t a = a0 + lane; a < a1; a += 32) {
+      int32_t v = col[a];
+      if (v < 0 || v >= n) {
+        bad |= kBadRange;
+        continue;
+      }
+      if (v == u) bad |= kSelfLoop;
+      if (a > a0 && col[a - 1] >= v) bad |= kUnsorted;
+      // symmetry: u must appear in N(v)
+      if (!contains_dev(col + rp[v], rp[v + 1] - rp[v], (int32_t)u)) bad |= kAsymmetric;
+    }
+  }
+  bad = __reduce_or_sync(kFull, bad);
+  if (lane == 0 && bad) atomicOr(flags, bad);
+}
+
+__device__ __forceinline__ bool keep_arc(int32_t u, int32_t du, int32_t v, int32_t dv) {
+  return du < dv || (du == dv && u < v);
+}
+
+// WRITE = false: out-degree per vertex; WRITE = true: compact kept arcs
+template <bool WRITE>
+__global__ void orient_kernel(int32_t n, const int32_t* __restrict__ rp,
+                              const int32_t* __restrict__ col, uint32_t* __restrict__ outdeg,
+                              const int64_t* __restrict__ dag_off, int32_t* __restrict__ dag_col) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t u = warp; u < n; u += nwarps) {
+    const int32_t a0 = rp[u], a1 = rp[u + 1];
+    const int32_t du = a1 - a0;
+    int64_t w = WRITE ? dag_off[u] : 0;
+    uint32_t c = 0;
+    for (int32_t a = a0; a < a1; a += 32) {
+      bool keep = false;
+      int32_t v = 0;
+      if (a + lane < a1) {
+        v = col[a + lane];
+        keep = keep_arc((int32_t)u, du, v, rp[v + 1] - rp[v]);
+      }
+      unsigned b = __ballot_sync(kFull, keep);
+      if (WRITE && keep) dag_col[w + __popc(b & ((1u << lane) - 1u))] = v;
+      w += __popc(b);
+      c += __popc(b);
+    }
+    if (!WRITE && lane == 0) outdeg[u] = c;
+  }
+}
+
+__global__ void narrow_kernel(const int64_t* __restrict__ in, int32_t* __restrict__ out, int64_t len) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len;
+       i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = (int32_t)in[i];
+}
+
+// up[v] = index of the first arc of v whose neighbour is greater than v
+__global__ void upper_kernel(int32_t n, const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
+                             int32_t* __restrict__ up) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+       v += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t a0 = rp[v], a1 = rp[v + 1];
+    up[v] = a0 + lower_bound_dev(col + a0, a1 - a0, (int32_t)v + 1);
+  }
+}
+
+static int warp_grid(int64_t items, int threads) {
+  int64_t blocks = (items * 32 + threads - 1) / threads;
+  int64_t cap = (int64_t)num_sms() * 16;
+  if (blocks > cap) blocks = cap;
+  return (int)std::max<int64_t>(blocks, 1);
+}
+
+// host-side repair: symmetrise, drop loops and duplicates, sort
+static void sanitize_host(int32_t n, const int64_t* rowptr, const int32_t* col,
+                          std::vector<int64_t>& rp_out, std::vector<int32_t>& col_out) {
+  std::vector<uint64_t> keys;
+  keys.reserve((size_t)rowptr[n] * 2);
+  for (int32_t u = 0; u < n; u++)
+    for (int64_t a = rowptr[u]; a < rowptr[u + 1]; a++) {
+      int32_t v = col[a];
+      if (v < 0 || v >= n || v == u) continue;
+      keys.push_back(((uint64_t)(uint32_t)u << 32) | (uint32_t)v);
+      keys.push_back(((uint64_t)(uint32_t)v << 32) | (uint32_t)u);
+    }
+  std::sort(keys.begin(), keys.end());
+  keys.erase(std::unique(keys.begin(), keys.end()), keys.end());
+  rp_out.assign((size_t)n + 1, 0);
+  col_out.resize(keys.size());
+  for (size_t i = 0; i < keys.size(); i++) {
+    rp_out[(keys[i] >> 32) + 1]++;
+    col_out[i] = (int32_t)(keys[i] & 0xffffffffu);
+  }
+  for (int32_t v = 0; v < n; v++) rp_out[v + 1] += rp_out[v];
+}
+
+void graph_free(Graph& g) {
+  if (g.rp) cudaFree(g.rp);
+  if (g.col) cudaFree(g.col);
+  if (g.dag_rp) cudaFree(g.dag_rp);
+  if (g.dag_col) cudaFree(g.dag_col);
+  if (g.gid) cudaFree(g.gid);
+  if (g.up) cudaFree(g.up);
+  g.rp = g.col = g.dag_rp = g.dag_col = g.gid = g.up = nullptr;
+  g.ws.release_all();
+  g.oriented = false;
+}
+
+pgm_status graph_upload(Graph& g, int32_t n, const int64_t* rowptr, const int32_t* col,
+                        bool rowptr_on_device, int64_t narcs, uint32_t flags, cudaStream_t s) {
+  if (n < 0 || !rowptr || (flags & ~(PGM_VALIDATE | PGM_SANITIZE))) {
+    set_error("graph: bad arguments (n=%d)", n);
+    return PGM_EINVAL;
+  }
+  g.stream = s;
+  g.n = n;
+  std::vector<int64_t> rp_s;
+  std::vector<int32_t> col_s;
+  std::vector<int64_t> h_rp;
+  if (!rowptr_on_device) {
+    if (rowptr[0] != 0) {
+      set_error("graph: rowptr[0] must be 0");
+      return PGM_EINVAL;
+    }
+    for (int32_t v = 0; v < n; v++)
+      if (rowptr[v + 1] < rowptr[v]) {
+        set_error("graph: rowptr decreases at vertex %d", v);
+        return PGM_EINVAL;
+      }
+    narcs = rowptr[n];
+    if (narcs > 0 && !col) {
+      set_error("graph: null col");
+      return PGM_EINVAL;
+    }
+    if (flags & PGM_SANITIZE) {
+      sanitize_host(n, rowptr, col, rp_s, col_s);
+      rowptr = rp_s.data();
+      col = col_s.data();
+      narcs = rowptr[n];
+    }
+    h_rp.assign(rowptr, rowptr + (size_t)n + 1);
+  } else {
+    if (flags & PGM_SANITIZE) {
+      set_error("graph: PGM_SANITIZE needs host arrays");
+      return PGM_EINVAL;
+    }
+    h_rp.resize((size_t)n + 1);
+    PGM_TRY_CUDA(cudaMemcpyAsync(h_rp.data(), rowptr, ((size_t)n + 1) * sizeof(int64_t),
+                                 cudaMemcpyDeviceToHost, s));
+    PGM_TRY_CUDA(cudaStreamSynchronize(s));
+    if (h_rp[0] != 0 || h_rp[n] != narcs) {
+      set_error("graph: device rowptr inconsistent with narcs");
+      return PGM_EINVAL;
+    }
+    for (int32_t v = 0; v < n; v++)
+      if (h_rp[v + 1] < h_rp[v]) {
+        set_error("graph: rowptr decreases at vertex %d", v);
+        return PGM_EINVAL;
+      }
+  }
+  if (narcs >= INT32_MAX) {
+    set_error("graph: %lld arcs exceed the int32 device index range", (long long)narcs);
+    return PGM_EUNSUPPORTED;
+  }
+  g.narcs = narcs;
+  std::vector<int32_t> rp32((size_t)n + 1);
+  int64_t dmax = 0;
+  for (int32_t v = 0; v <= n; v++) rp32[v] = (int32_t)h_rp[v];
+  for (int32_t v = 0; v < n; v++) dmax = std::max(dmax, h_rp[v + 1] - h_rp[v]);
+  g.dmax = dmax;
+  PGM_TRY_CUDA(cudaMalloc(&g.rp, ((size_t)n + 1) * sizeof(int32_t)));
+  PGM_TRY_CUDA(cudaMalloc(&g.col, (size_t)std::max<int64_t>(narcs, 1) * sizeof(int32_t)));
+  PGM_TRY_CUDA(cudaMemcpyAsync(g.rp, rp32.data(), ((size_t)n + 1) * sizeof(int32_t),
+                               cudaMemcpyHostToDevice, s));
+  if (narcs > 0)
+    PGM_TRY_CUDA(cudaMemcpyAsync(g.col, col, (size_t)narcs * sizeof(int32_t),
+                                 rowptr_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                 s));
+  g.h_rp.swap(h_rp);
+  if ((flags & PGM_VALIDATE) && n > 0) {
+    PGM_TRY(g.ws.ctr.reserve(16));
+    unsigned* fl = reinterpret_cast<unsigned*>(g.ws.ctr.p);
+    PGM_TRY_CUDA(cudaMemsetAsync(fl, 0, sizeof(unsigned), s));
+    validate_kernel<<<warp_grid(n, 256), 256, 0, s>>>(n, g.rp, g.col, fl);
+    PGM_CHECK_LAUNCH();
+    unsigned hf = 0;
+    PGM_TRY_CUDA(cudaMemcpyAsync(&hf, fl, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+    PGM_TRY_CUDA(cudaStreamSynchronize(s));
+    if (hf) {
+      set_error("graph: invalid CSR:%s%s%s%s", (hf & kBadRange) ? " neighbour-out-of-range" : "",
+                (hf & kUnsorted) ? " unsorted-or-duplicate" : "", (hf & kSelfLoop) ? " self-loop" : "",
+                (hf & kAsymmetric) ? " asymmetric" : "");
+      return PGM_EINVAL;
+    }
+  }
+  PGM_TRY_CUDA(cudaStreamSynchronize(s));
+  return PGM_OK;
+}
+
+pgm_status graph_orient(Graph& g) {
+  if (g.oriented) return PGM_OK;
+  cudaStream_t s = g.stream;
+  const int32_t n = g.n;
+  const int64_t m = g.narcs / 2;
+  if (g.narcs % 2) {
+    set_error("orient: odd number of arcs (input not symmetric)");
+    return PGM_EINVAL;
+  }
+  if (!g.dag_rp) PGM_TRY_CUDA(cudaMalloc(&g.dag_rp, ((size_t)n + 1) * sizeof(int32_t)));
+  if (!g.dag_col) PGM_TRY_CUDA(cudaMalloc(&g.dag_col, (size_t)std::max<int64_t>(m, 1) * sizeof(int32_t)));
+  PGM_TRY(g.ws.cnt[0].reserve((size_t)n + 1));
+  PGM_TRY(g.ws.off[0].reserve((size_t)n + 1));
+  Profiler& prof = profiler();
+  int id = prof.begin("orient", 1);
+  if (n > 0) {
+    orient_kernel<false><<<warp_grid(n, 256), 256, 0, s>>>(n, g.rp, g.col, g.ws.cnt[0].p, nullptr,
+                                                           nullptr);
+    PGM_CHECK_LAUNCH();
+  }
+  PGM_TRY(exclusive_scan(g.ws.cnt[0].p, n, g.ws.off[0].p, g.ws, s));
+  g.h_dag_rp.resize((size_t)n + 1);
+  PGM_TRY_CUDA(cudaMemcpyAsync(g.h_dag_rp.data(), g.ws.off[0].p, ((size_t)n + 1) * sizeof(int64_t),
+                               cudaMemcpyDeviceToHost, s));
+  PGM_TRY_CUDA(cudaStreamSynchronize(s));
+  if (g.h_dag_rp[n] != m) {
+    // not symmetric: the kept-arc count differs from m; refuse before writing
+    set_error("orient: kept %lld arcs, expected %lld (input not symmetric?)",
+              (long long)g.h_dag_rp[n], (long long)m);
+    return PGM_EINVAL;
+  }
+  if (n > 0) {
+    orient_kernel<true><<<warp_grid(n, 256), 256, 0, s>>>(n, g.rp, g.col, nullptr, g.ws.off[0].p,
+                                                          g.dag_col);
+    PGM_CHECK_LAUNCH();
+  }
+  narrow_kernel<<<std::max(1, std::min(num_sms() * 8, (int)((n + 256) / 256))), 256, 0, s>>>(
+      g.ws.off[0].p, g.dag_rp, (int64_t)n + 1);
+  PGM_CHECK_LAUNCH();
+  prof.end(id, (double)n, 8.0 * (double)g.narcs);
+  PGM_TRY_CUDA(cudaStreamSynchronize(s));
+  int64_t dd = 0;
+  for (int32_t v = 0; v < n; v++) dd = std::max(dd, g.h_dag_rp[v + 1] - g.h_dag_rp[v]);
+  g.dag_dmax = dd;
+  g.oriented = true;
+  return PGM_OK;
+}
+
+pgm_status graph_prepare_motifs(Graph& g) {
+  if (g.up) return PGM_OK;
+  PGM_TRY_CUDA(cudaMalloc(&g.up, ((size_t)g.n + 1) * sizeof(int32_t)));
+  if (g.n > 0) {
+    const int blocks = std::max(1, std::min(num_sms() * 8, (g.n + 255) / 256));
+    upper_kernel<<<blocks, 256, 0, g.stream>>>(g.n, g.rp, g.col, g.up);
+    PGM_CHECK_LAUNCH();
+  }
+  PGM_TRY_CUDA(cudaStreamSynchronize(g.stream));
+  return PGM_OK;
+}
+
+}  // namespace pgm
+
+// ------------------------------------------------------------------- C ABI
+extern "C" {
+
+pgm_status pgm_graph_create_csr(int32_t n, const int64_t* rowptr, const int32_t* col, uint32_t flags,
+                                void* stream, pgm_graph** out) {
+  if (!out) {
+    pgm::set_error("pgm_graph_create_csr: null out");
+    return PGM_EINVAL;
+  }
+  pgm_graph* h = new (std::nothrow) pgm_graph();
+  if (!h) return PGM_ENOMEM;
+  pgm::profiler().start((cudaStream_t)stream);
+  pgm_status st = pgm::graph_upload(h->g, n, rowptr, col, false, 0, flags, (cudaStream_t)stream);
+  if (st != PGM_OK) {
+    pgm::graph_free(h->g);
+    delete h;
+    return st;
+  }
+  *out = h;
+  return PGM_OK;
+}
+
+pgm_status pgm_graph_create_csr_dev(int32_t n, const int64_t* rowptr_dev, const int32_t* col_dev,
+                                    int64_t narcs, uint32_t flags, void* stream, pgm_graph** out) {
+  if (!out || (narcs > 0 && !col_dev)) {
+    pgm::set_error("pgm_graph_create_csr_dev: bad arguments");
+    return PGM_EINVAL;
+  }
+  pgm_graph* h = new (std::nothrow) pgm_graph();
+  if (!h) return PGM_ENOMEM;
+  pgm::profiler().start((cudaStream_t)stream);
+  pgm_status st = pgm::graph_upload(h->g, n, rowptr_dev, col_dev, true, narcs, flags,
+                                    (cudaStream_t)stream);
+  if (st != PGM_OK) {
+    pgm::graph_free(h->g);
+    delete h;
+    return st;
+  }
+  *out = h;
+  return PGM_OK;
+}
+
+pgm_status pgm_graph_orient_by_degree(pgm_graph* g) {
+  if (!g) {
+    pgm::set_error("pgm_graph_orient_by_degree: null graph");
+    return PGM_EINVAL;
+  }
+  pgm::profiler().start(g->g.stream);
+  return pgm::graph_orient(g->g);
+}
+
+pgm_status pgm_graph_stats_get(const pgm_graph* gh, pgm_graph_stats* out) {
+  if (!gh || !out) {
+    pgm::set_error("pgm_graph_stats_get: null argument");
+    return PGM_EINVAL;
+  }
+  const pgm::Graph& g = gh->g;
+  unsigned __int128 s2 = 0, s3 = 0;
+  for (int32_t v = 0; v < g.n; v++) {
+    unsigned __int128 d = (unsigned __int128)(g.h_rp[v + 1] - g.h_rp[v]);
+    if (d >= 2) s2 += d * (d - 1) / 2;
+    if (d >= 3) s3 += d * (d - 1) * (d - 2) / 6;
+  }
+  pgm_graph_stats r;
+  memset(&r, 0, sizeof(r));
+  r.n = g.n;
+  r.m = g.narcs / 2;
+  r.dmax = g.dmax;
+  r.dag_dmax = g.oriented ? g.dag_dmax : 0;
+  r.sum_c2[0] = (uint64_t)s2;
+  r.sum_c2[1] = (uint64_t)(s2 >> 64);
+  r.sum_c3[0] = (uint64_t)s3;
+  r.sum_c3[1] = (uint64_t)(s3 >> 64);
+  *out = r;
+  return PGM_OK;
+}
+
+void pgm_graph_destroy(pgm_graph* g) {
+  if (!g) return;
+  cudaStreamSynchronize(g->g.stream);
+  pgm::graph_free(g->g);
+  delete g;
+}
+
+}  // extern "C"

@@ -1,0 +1,779 @@
+// motif.cu -- vertex-induced 3- and 4-motif counting (Sec. 3.3 Listing 4,
+// Sec. 4.2 memoization and customised pattern classification).
+//
+// Embeddings grow by a neighbour of ANY vertex (Sec. 3.1, Algorithm 2), and a
+// canonical test keeps one copy of every connected vertex set (Sec. 3.2).
+// The paper does not print its canonical rule; this build uses the
+// breadth-first canonical order: v0 = min(S), and each next vertex is the
+// unused vertex adjacent to the prefix with the smallest key (f(u), u), where
+// f(u) is the index of u's first neighbour in the prefix.  Keys of a
+// canonical sequence are strictly increasing, so appending u to a canonical
+// prefix (v0..v_{i-1}) is canonical iff u > v0 and either f(u) = i-1 or
+// (f(v_{i-1}), v_{i-1}) < (f(u), u).
+//
+// Level 2: edges (v0, v1), v0 < v1, grouped by v0: segment A(v0) = the
+// neighbours of v0 above v0.  Level 3 children of (v0, v1):
+//   f2 = 0: u in N(v0), u > v1                    (u adjacent to v0)
+//   f2 = 1: u in N(v1), u > v0, u not in N(v0)    (u adjacent to v1 only)
+// stored as vid | a02 << 30 | a12 << 31 (memoised pattern of the 3-vertex
+// embedding: a02 = v2~v0, a12 = v2~v1; Sec. 4.2 memoization).
+// 3-motif pattern: triangle iff a02 & a12 (Listing 6), else wedge.
+//
+// Last level (fused count, never materialised): for a 3-embedding
+// (v0, v1, v2) the 4th vertex w > v0 with adjacency mask M = (w~v0, w~v1,
+// w~v2) is accepted by the canonical test iff
+//   f2 = 0: M has bit 0 -> w > v2;  otherwise -> always;
+//   f2 = 1: M has bit 0 -> never;   M in {2, 6} -> w > v2;  M = 4 -> always.
+// The pattern follows from (a02, a12, M): edge count and maximum degree
+// (customised classification, Listing 6 extended to 4 vertices):
+//   3 edges: 3-star (max degree 3) or 4-path; 4 edges: tailed triangle
+//   (max degree 3) or 4-cycle; 5: diamond; 6: 4-clique.
+// Candidates adjacent to v2 are enumerated from N(v2) and looked up in the
+// parent's lists A = N(v0) & (v0, inf) and B = N(v1) & (v0, inf) (binary
+// search, Sec. 5.4); candidates adjacent only to v0 and/or v1 are counted
+// by rank queries on A, B and I = A & B, minus the ones seen in N(v2).
+#include <algorithm>
+#include <cstring>
+
+#include "common.cuh"
+
+namespace pgm {
+
+namespace {
+
+enum MMode : int { mCount = 0, mWrite = 1, mSum = 2 };
+constexpr int kMGrab = 2;
+constexpr uint32_t kVidMask = (1u << 30) - 1u;
+constexpr uint32_t kA02 = 1u << 30;
+constexpr uint32_t kA12 = 1u << 31;
+
+// 4-vertex pattern of a 3-embedding with memo (a02, a12) (edge v0-v1
+// always present) plus a vertex with adjacency mask M (bit j = adjacent to
+// v_j); -1 if M = 0.  Order: 3-star, 4-path, tailed-triangle, 4-cycle,
+// diamond, 4-clique.
+__device__ __forceinline__ int pattern4(int a02, int a12, int M) {
+  const int m0 = M & 1, m1 = (M >> 1) & 1, m2 = (M >> 2) & 1;
+  const int d0 = 1 + a02 + m0, d1 = 1 + a12 + m1, d2 = a02 + a12 + m2, d3 = m0 + m1 + m2;
+  const int edges = 1 + a02 + a12 + d3;
+  const int dm = max(max(d0, d1), max(d2, d3));
+  if (d3 == 0) return -1;
+  switch (edges) {
+    case 3: return dm == 3 ? 0 : 1;
+    case 4: return dm == 3 ? 2 : 3;
+    case 5: return 4;
+    default: return 5;
+  }
+}
+
+struct MotifArgs {
+  const int32_t* rp;   // undirected CSR
+  const int32_t* col;
+  const int32_t* up;   // up[v] = first arc of v whose neighbour is > v
+  int32_t v_lo, v_hi;  // parent (v0) range
+  int64_t a_base;      // arc index that maps to entry 0 (entries are arcs)
+  uint32_t* cnt;       // mCount: children per arc (index a - a_base)
+  const int64_t* off;  // mWrite / level 3: exclusive scan of cnt
+  int64_t off_shift;   // subtracted from off -> index into l3
+  uint32_t* l3;        // mWrite output / level-3 input
+  unsigned long long* acc;        // pattern counts (2 or 6)
+  unsigned long long* per_graph;  // per-graph counts (batches) or nullptr
+  const int32_t* gid;
+  unsigned long long* stat;   // elements examined (algorithmic bytes)
+  unsigned long long* queue;  // [0] warp queue [1] block queue [2] hub count
+  unsigned long long* err;    // non-zero: a hub vertex could not be queued
+  int32_t* big;
+  int64_t big_cap;
+  int cap;        // per-warp staging capacity (ints) per list
+  int block_cap;  // per-block staging capacity for A
+  int32_t* scratch;  // per-warp global scratch (block kernel), scratch_stride ints each
+  int64_t scratch_stride;
+};
+
+template <int N>
+__device__ __forceinline__ void flush_patterns(const MotifArgs& P, long long (&c)[N], int g,
+                                               int lane) {
+#pragma unroll
+  for (int i = 0; i < N; i++) {
+    long long s = warp_sum(c[i]);
+    if (lane == 0 && s) {
+      unsigned long long* dst = (P.per_graph && g >= 0) ? P.per_graph + (int64_t)g * N : P.acc;
+      atomicAdd(dst + i, (unsigned long long)s);
+    }
+    c[i] = 0;
+  }
+}
+
+template <int N>
+__device__ __forceinline__ void add_pat(long long (&c)[N], int p, long long d) {
+#pragma unroll
+  for (int i = 0; i < N; i++) c[i] += (i == p) ? d : 0;
+}
+
+// ------------------------------------------------------ level 2 -> 3 / 3-motif
+// Entries j0..j0+31 of v0's segment A (length s).  For entry j (v1 = A[j])
+// scan N(v1): x > v0 and not in A -> f2=1 child; x in A and x > v1 -> the
+// f2=0 child x is a triangle (a12 = 1).
+template <int MODE>
+__device__ __forceinline__ void l2_batch(const MotifArgs& P, const int32_t* A, int s, int j0,
+                                         int32_t v0, int64_t arc0, int lane, uint32_t* wcnt,
+                                         long long (&c)[2], unsigned long long& seen) {
+  const int j = j0 + lane;
+  const bool valid = j < s;
+  int32_t v1 = 0, a0 = 0, len = 0;
+  if (valid) {
+    v1 = A[j];
+    a0 = P.rp[v1];
+    len = P.rp[v1 + 1] - a0;
+  }
+  seen += (unsigned long long)len;
+  const int incl = warp_inclusive_scan(len, lane);
+  const int total = __shfl_sync(kFull, incl, 31);
+  const int excl = incl - len;
+  int64_t my_off = 0;
+  if (MODE == mSum && valid) c[0] += s - j - 1;  // f2 = 0 children start as wedges
+  if (MODE != mSum) {
+    wcnt[lane] = 0;
+    if (MODE == mWrite && valid) my_off = P.off[arc0 + j] - P.off_shift;
+    __syncwarp();
+  }
+  if (MODE == mWrite) {
+    // phase 1: the f2 = 0 block A[j+1..s) with a02 = 1, a12 = 0
+    for (int q = 0; q < 32; q++) {
+      const int jq = j0 + q;
+      if (jq >= s) break;
+      const int64_t oq = __shfl_sync(kFull, my_off, q);
+      for (int i = jq + 1 + lane; i < s; i += 32) P.l3[oq + (i - jq - 1)] = (uint32_t)A[i] | kA02;
+    }
+    __syncwarp();
+  }
+  const int32_t amin = A[0], amax = A[s - 1];
+  for (int base = 0; base < total; base += 32) {
+    const int t = base + lane;
+    const bool active = t < total;
+    const int q = min(warp_owner(incl, t), 31);
+    const int aq = __shfl_sync(kFull, a0, q);
+    const int eq = __shfl_sync(kFull, excl, q);
+    const int32_t v1q = __shfl_sync(kFull, v1, q);
+    bool child = false, tri = false;
+    int32_t x = 0;
+    int xi = 0;
+    if (active) {
+      x = P.col[aq + (t - eq)];
+      if (x > v0) {
+        bool inA = false;
+        if (x >= amin && x <= amax) {
+          xi = lower_bound_dev(A, s, x);
+          inA = xi < s && A[xi] == x;
+        }
+        child = !inA;
+        tri = inA && x > v1q;
+      }
+    }
+    if (MODE == mSum) {
+      c[0] += (child ? 1 : 0) - (tri ? 1 : 0);
+      c[1] += tri ? 1 : 0;
+    } else {
+      const unsigned b = __ballot_sync(kFull, child);
+      const int first = max(eq - base, 0);
+      const unsigned from_first = ~((1u << first) - 1u);
+      const unsigned upto_me = lane == 31 ? kFull : ((2u << lane) - 1u);
+      if (MODE == mWrite) {
+        const int64_t oq = __shfl_sync(kFull, my_off, q);
+        const int jq = j0 + q;
+        const uint32_t rq = wcnt[q];
+        if (child)
+          P.l3[oq + (s - jq - 1) + rq + __popc(b & from_first & ((1u << lane) - 1u))] = (uint32_t)x | kA12;
+        if (tri) P.l3[oq + (xi - jq - 1)] = (uint32_t)x | kA02 | kA12;
+      }
+      const int qn = __shfl_down_sync(kFull, q, 1);
+      const bool last = active && (lane == 31 || t + 1 >= total || qn != q);
+      __syncwarp();
+      if (last) wcnt[q] += __popc(b & from_first & upto_me);
+      __syncwarp();
+    }
+  }
+  if (MODE == mCount) {
+    if (valid) P.cnt[arc0 + j] = wcnt[lane] + (uint32_t)(s - j - 1);
+    __syncwarp();
+  }
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(512) motif_l2_warp(MotifArgs P) {
+  extern __shared__ int32_t smem[];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int32_t* A = smem + wid * (P.cap + 32);
+  uint32_t* wcnt = reinterpret_cast<uint32_t*>(A + P.cap);
+  long long c[2] = {0, 0};
+  unsigned long long seen = 0;
+  int cur_g = -1;
+  const int64_t np = (int64_t)P.v_hi - P.v_lo;
+  for (;;) {
+    unsigned long long p0 = 0;
+    if (lane == 0) p0 = atomicAdd(P.queue, (unsigned long long)kMGrab);
+    p0 = __shfl_sync(kFull, p0, 0);
+    if ((int64_t)p0 >= np) break;
+    const int64_t pend = min((int64_t)p0 + kMGrab, np);
+    for (int64_t pi = (int64_t)p0; pi < pend; pi++) {
+      const int32_t v0 = (int32_t)(P.v_lo + pi);
+      const int32_t u0 = P.up[v0], u1 = P.rp[v0 + 1];
+      const int s = u1 - u0;
+      if (s < 1) continue;
+      if (s > P.cap) {
+        if (lane == 0) {
+          unsigned long long i = atomicAdd(P.queue + 2, 1ull);
+          if ((int64_t)i < P.big_cap)
+            P.big[i] = v0;
+          else
+            atomicAdd(P.err, 1ull);  // cannot happen: every vertex fits
+        }
+        continue;
+      }
+      for (int i = lane; i < s; i += 32) A[i] = P.col[u0 + i];
+      __syncwarp();
+      if (MODE == mSum && P.gid) {
+        const int g = P.gid[v0];
+        if (g != cur_g) {
+          flush_patterns<2>(P, c, cur_g, lane);
+          cur_g = g;
+        }
+      }
+      const int64_t arc0 = (int64_t)u0 - P.a_base;
+      for (int j0 = 0; j0 < s; j0 += 32) l2_batch<MODE>(P, A, s, j0, v0, arc0, lane, wcnt, c, seen);
+      __syncwarp();
+    }
+  }
+  if (MODE == mSum) flush_patterns<2>(P, c, cur_g, lane);
+  seen = warp_sum(seen);
+  if (lane == 0 && seen) atomicAdd(P.stat, seen);
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(512) motif_l2_block(MotifArgs P) {
+  extern __shared__ int32_t smem[];
+  __shared__ long long sh_idx;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  int32_t* stage = smem;
+  uint32_t* wcnt = reinterpret_cast<uint32_t*>(smem + P.block_cap) + wid * 32;
+  long long c[2] = {0, 0};
+  unsigned long long seen = 0;
+  int cur_g = -1;
+  const long long nbig = min((long long)P.queue[2], (long long)P.big_cap);
+  for (;;) {
+    if (threadIdx.x == 0) sh_idx = (long long)atomicAdd(P.queue + 1, 1ull);
+    __syncthreads();
+    const long long idx = sh_idx;
+    __syncthreads();
+    if (idx >= nbig) break;
+    const int32_t v0 = P.big[idx];
+    const int32_t u0 = P.up[v0], u1 = P.rp[v0 + 1];
+    const int s = u1 - u0;
+    const int32_t* A;
+    if (s <= P.block_cap) {
+      for (int i = threadIdx.x; i < s; i += blockDim.x) stage[i] = P.col[u0 + i];
+      A = stage;
+    } else {
+      A = P.col + u0;
+    }
+    __syncthreads();
+    if (MODE == mSum && P.gid) {
+      const int g = P.gid[v0];
+      if (g != cur_g) {
+        flush_patterns<2>(P, c, cur_g, lane);
+        cur_g = g;
+      }
+    }
+    const int64_t arc0 = (int64_t)u0 - P.a_base;
+    for (int j0 = wid * 32; j0 < s; j0 += nw * 32)
+      l2_batch<MODE>(P, A, s, j0, v0, arc0, lane, wcnt, c, seen);
+    __syncthreads();
+  }
+  if (MODE == mSum) flush_patterns<2>(P, c, cur_g, lane);
+  seen = warp_sum(seen);
+  if (lane == 0 && seen) atomicAdd(P.stat, seen);
+}
+
+// ------------------------------------------------------------- level 3 (last)
+// One edge (v0, v1 = A[j]): B = N(v1) & (v0, inf), I = A & B, then the
+// children of the edge from the level-3 list.
+__device__ __forceinline__ void l3_edge(const MotifArgs& P, const int32_t* A, int s, int j,
+                                        int32_t v0, int64_t arc0, int lane, int32_t* Bbuf,
+                                        int32_t* Ibuf, long long (&c)[6],
+                                        unsigned long long& seen) {
+  const int32_t v1 = A[j];
+  const int64_t cb = P.off[arc0 + j] - P.off_shift;
+  const int64_t ce = P.off[arc0 + j + 1] - P.off_shift;
+  if (ce <= cb) return;
+  // B: suffix of N(v1) above v0
+  const int32_t r0 = P.rp[v1], r1 = P.rp[v1 + 1];
+  int bstart = 0;
+  if (lane == 0) bstart = lower_bound_dev(P.col + r0, r1 - r0, v0 + 1);
+  bstart = __shfl_sync(kFull, bstart, 0);
+  const int nb = r1 - r0 - bstart;
+  const int32_t* B;
+  if (nb <= P.cap) {
+    for (int i = lane; i < nb; i += 32) Bbuf[i] = P.col[r0 + bstart + i];
+    B = Bbuf;
+  } else {
+    B = P.col + r0 + bstart;
+  }
+  __syncwarp();
+  // I = A & B (sorted): iterate the shorter list, search the longer one
+  int ni = 0;
+  {
+    const bool iterA = s <= nb;
+    const int32_t* X = iterA ? A : B;
+    const int32_t* Y = iterA ? B : A;
+    const int nx = iterA ? s : nb, ny = iterA ? nb : s;
+    for (int i0 = 0; i0 < nx; i0 += 32) {
+      const int i = i0 + lane;
+      bool in = false;
+      int32_t x = 0;
+      if (i < nx) {
+        x = X[i];
+        in = contains_dev(Y, ny, x);
+      }
+      const unsigned b = __ballot_sync(kFull, in);
+      if (in) Ibuf[ni + __popc(b & ((1u << lane) - 1u))] = x;
+      ni += __popc(b);
+    }
+  }
+  __syncwarp();
+  if (lane == 0) seen += (unsigned long long)(nb + s);
+  const int32_t amin = A[0], amax = A[s - 1];
+  const int32_t bmin = nb > 0 ? B[0] : 0, bmax = nb > 0 ? B[nb - 1] : -1;
+  // children, 32 at a time
+  for (int64_t c0 = cb; c0 < ce; c0 += 32) {
+    const int64_t ci = c0 + lane;
+    const bool valid = ci < ce;
+    int32_t v2 = 0, a0 = 0, len = 0;
+    int a02 = 0, a12 = 0;
+    if (valid) {
+      const uint32_t e = P.l3[ci];
+      v2 = (int32_t)(e & kVidMask);
+      a02 = (e & kA02) ? 1 : 0;
+      a12 = (e & kA12) ? 1 : 0;
+      a0 = P.rp[v2];
+      len = P.rp[v2 + 1] - a0;
+      // base counts of candidates not adjacent to v2 (rank queries)
+      const long long I_gt2 = ni - lower_bound_dev(Ibuf, ni, v2 + 1);  // |I & (v2, inf)|
+      if (a02) {
+        const int ia = lower_bound_dev(A, s, v2);  // v2 = A[ia]
+        const long long A_gt2 = s - ia - 1;        // v1 < v2, so v1 is not counted
+        add_pat<6>(c, pattern4(1, a12, 1), A_gt2 - I_gt2);        // A only, w > v2
+        add_pat<6>(c, pattern4(1, a12, 3), I_gt2);                // A & B, w > v2
+        add_pat<6>(c, pattern4(1, a12, 2), (long long)(nb - ni));  // B only, w > v0
+      } else {
+        const int ib = lower_bound_dev(B, nb, v2 + 1);
+        const long long B_gt2 = nb - ib;
+        add_pat<6>(c, pattern4(0, 1, 2), B_gt2 - I_gt2);  // B only, w > v2
+      }
+    }
+    seen += (unsigned long long)len;
+    const int incl = warp_inclusive_scan(len, lane);
+    const int total = __shfl_sync(kFull, incl, 31);
+    const int excl = incl - len;
+    for (int base = 0; base < total; base += 32) {
+      const int t = base + lane;
+      const bool active = t < total;
+      const int q = min(warp_owner(incl, t), 31);
+      const int aq = __shfl_sync(kFull, a0, q);
+      const int eq = __shfl_sync(kFull, excl, q);
+      const int32_t v2q = __shfl_sync(kFull, v2, q);
+      const int a02q = __shfl_sync(kFull, a02, q);
+      const int a12q = __shfl_sync(kFull, a12, q);
+      if (active) {
+        const int32_t w = P.col[aq + (t - eq)];
+        if (w > v0 && w != v1) {
+          const int a = (w >= amin && w <= amax && contains_dev(A, s, w)) ? 1 : 0;
+          const int b = (w >= bmin && w <= bmax && contains_dev(B, nb, w)) ? 1 : 0;
+          const int M = 4 | a | (b << 1);
+          if (!a && !b) {
+            add_pat<6>(c, pattern4(a02q, a12q, 4), 1);
+          } else if (a02q) {
+            if (!a || w > v2q) {  // adjacent to v0: needs w > v2; to v1 only: always
+              add_pat<6>(c, pattern4(1, a12q, M), 1);
+              add_pat<6>(c, pattern4(1, a12q, M & 3), -1);
+            }
+          } else if (!a && w > v2q) {  // f2 = 1, adjacent to v1 (and v2) only
+            add_pat<6>(c, pattern4(0, 1, M), 1);
+            add_pat<6>(c, pattern4(0, 1, M & 3), -1);
+          }
+        }
+      }
+    }
+  }
+}
+
+__global__ void __launch_bounds__(512) motif_l3_warp(MotifArgs P) {
+  extern __shared__ int32_t smem[];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int32_t* A = smem + (int64_t)wid * 3 * P.cap;
+  int32_t* Bbuf = A + P.cap;
+  int32_t* Ibuf = Bbuf + P.cap;
+  long long c[6] = {0, 0, 0, 0, 0, 0};
+  unsigned long long seen = 0;
+  int cur_g = -1;
+  const int64_t np = (int64_t)P.v_hi - P.v_lo;
+  for (;;) {
+    unsigned long long p0 = 0;
+    if (lane == 0) p0 = atomicAdd(P.queue, (unsigned long long)kMGrab);
+    p0 = __shfl_sync(kFull, p0, 0);
+    if ((int64_t)p0 >= np) break;
+    const int64_t pend = min((int64_t)p0 + kMGrab, np);
+    for (int64_t pi = (int64_t)p0; pi < pend; pi++) {
+      const int32_t v0 = (int32_t)(P.v_lo + pi);
+      const int32_t u0 = P.up[v0], u1 = P.rp[v0 + 1];
+      const int s = u1 - u0;
+      if (s < 1) continue;
+      const int64_t arc0 = (int64_t)u0 - P.a_base;
+      if (P.off[arc0 + s] - P.off[arc0] == 0) continue;  // no level-3 entries below v0
+      if (s > P.cap) {
+        if (lane == 0) {
+          unsigned long long i = atomicAdd(P.queue + 2, 1ull);
+          if ((int64_t)i < P.big_cap)
+            P.big[i] = v0;
+          else
+            atomicAdd(P.err, 1ull);  // cannot happen: every vertex fits
+        }
+        continue;
+      }
+      for (int i = lane; i < s; i += 32) A[i] = P.col[u0 + i];
+      __syncwarp();
+      if (P.gid) {
+        const int g = P.gid[v0];
+        if (g != cur_g) {
+          flush_patterns<6>(P, c, cur_g, lane);
+          cur_g = g;
+        }
+      }
+      for (int j = 0; j < s; j++) l3_edge(P, A, s, j, v0, arc0, lane, Bbuf, Ibuf, c, seen);
+      __syncwarp();
+    }
+  }
+  flush_patterns<6>(P, c, cur_g, lane);
+  seen = warp_sum(seen);
+  if (lane == 0 && seen) atomicAdd(P.stat, seen);
+}
+
+__global__ void __launch_bounds__(512) motif_l3_block(MotifArgs P) {
+  extern __shared__ int32_t smem[];
+  __shared__ long long sh_idx;
+  __shared__ int sh_edge;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  int32_t* stage = smem;
+  int32_t* Bbuf = smem + P.block_cap + (int64_t)wid * P.cap;
+  int32_t* Ibuf = P.scratch + ((int64_t)blockIdx.x * nw + wid) * P.scratch_stride;
+  long long c[6] = {0, 0, 0, 0, 0, 0};
+  unsigned long long seen = 0;
+  int cur_g = -1;
+  const long long nbig = min((long long)P.queue[2], (long long)P.big_cap);
+  for (;;) {
+    if (threadIdx.x == 0) {
+      sh_idx = (long long)atomicAdd(P.queue + 1, 1ull);
+      sh_edge = 0;
+    }
+    __syncthreads();
+    const long long idx = sh_idx;
+    if (idx >= nbig) break;
+    const int32_t v0 = P.big[idx];
+    const int32_t u0 = P.up[v0], u1 = P.rp[v0 + 1];
+    const int s = u1 - u0;
+    const int32_t* A;
+    if (s <= P.block_cap) {
+      for (int i = threadIdx.x; i < s; i += blockDim.x) stage[i] = P.col[u0 + i];
+      A = stage;
+    } else {
+      A = P.col + u0;
+    }
+    __syncthreads();
+    if (P.gid) {
+      const int g = P.gid[v0];
+      if (g != cur_g) {
+        flush_patterns<6>(P, c, cur_g, lane);
+        cur_g = g;
+      }
+    }
+    const int64_t arc0 = (int64_t)u0 - P.a_base;
+    for (;;) {
+      int j = 0;
+      if (lane == 0) j = atomicAdd(&sh_edge, 1);
+      j = __shfl_sync(kFull, j, 0);
+      if (j >= s) break;
+      l3_edge(P, A, s, j, v0, arc0, lane, Bbuf, Ibuf, c, seen);
+    }
+    __syncthreads();
+  }
+  flush_patterns<6>(P, c, cur_g, lane);
+  seen = warp_sum(seen);
+  if (lane == 0 && seen) atomicAdd(P.stat, seen);
+}
+
+constexpr int kQ = 0, kErr = 7, kAcc = 8, kStat = 16, kNSlots = 32;
+
+struct MotifRun {
+  Graph& g;
+  Workspace& ws;
+  cudaStream_t s;
+  int k;
+  const pgm_options o;
+  int cap, block_cap;
+  unsigned long long* per_graph = nullptr;
+  double l3_size = 0;
+  int chunks = 0;
+  MotifRun(Graph& g_, Workspace& ws_, cudaStream_t s_, int k_)
+      : g(g_), ws(ws_), s(s_), k(k_), o(options()) {
+    cap = o.warp_stage_cap;
+    block_cap = 16384;
+  }
+  unsigned long long* ctr() { return ws.ctr.p; }
+
+  MotifArgs args(int32_t v_lo, int32_t v_hi) {
+    MotifArgs P;
+    memset(&P, 0, sizeof(P));
+    P.rp = g.rp;
+    P.col = g.col;
+    P.up = g.up;
+    P.v_lo = v_lo;
+    P.v_hi = v_hi;
+    P.a_base = g.h_rp[v_lo];
+    P.acc = ctr() + kAcc;
+    P.per_graph = per_graph;
+    P.gid = g.gid;
+    P.queue = ctr() + kQ;
+    P.err = ctr() + kErr;
+    P.big = reinterpret_cast<int32_t*>(ws.big.p);
+    P.big_cap = (int64_t)ws.big.cap * 2;
+    P.cap = cap;
+    P.block_cap = block_cap;
+    return P;
+  }
+
+  template <int MODE>
+  pgm_status launch_l2(MotifArgs P, const char* name) {
+    PGM_TRY_CUDA(cudaMemsetAsync(ctr() + kQ, 0, 4 * sizeof(unsigned long long), s));
+    P.stat = ctr() + kStat + MODE;
+    const int threads = o.block_threads;
+    const size_t wsmem = (size_t)(threads / 32) * (cap + 32) * sizeof(int32_t);
+    const size_t bsmem = (size_t)block_cap * sizeof(int32_t) + 16 * 32 * sizeof(uint32_t);
+    PGM_TRY(smem_attr((const void*)motif_l2_warp<MODE>, 160 * 1024));
+    PGM_TRY(smem_attr((const void*)motif_l2_block<MODE>, 160 * 1024));
+    const int64_t np = (int64_t)P.v_hi - P.v_lo;
+    int wgrid = grid_for((const void*)motif_l2_warp<MODE>, threads, wsmem);
+    const int64_t blocks_needed = ((np + kMGrab - 1) / kMGrab + threads / 32 - 1) / (threads / 32);
+    wgrid = (int)std::max<int64_t>(1, std::min<int64_t>(wgrid, blocks_needed));
+    const int bgrid = grid_for((const void*)motif_l2_block<MODE>, 512, bsmem);
+    Profiler& prof = profiler();
+    int id = prof.begin(name, 2);
+    motif_l2_warp<MODE><<<wgrid, threads, wsmem, s>>>(P);
+    PGM_CHECK_LAUNCH();
+    motif_l2_block<MODE><<<bgrid, 512, bsmem, s>>>(P);
+    PGM_CHECK_LAUNCH();
+    prof.end(id, (double)(g.h_rp[P.v_hi] - g.h_rp[P.v_lo]) / 2.0, 0.0);
+    return PGM_OK;
+  }
+
+  pgm_status launch_l3(MotifArgs P, double entries) {
+    PGM_TRY_CUDA(cudaMemsetAsync(ctr() + kQ, 0, 4 * sizeof(unsigned long long), s));
+    P.stat = ctr() + kStat + 3;
+    const int threads = o.block_threads;
+    const size_t wsmem = (size_t)(threads / 32) * 3 * cap * sizeof(int32_t);
+    const size_t bsmem = ((size_t)block_cap + 16 * (size_t)cap) * sizeof(int32_t);
+    PGM_TRY(smem_attr((const void*)motif_l3_warp, 200 * 1024));
+    PGM_TRY(smem_attr((const void*)motif_l3_block, 200 * 1024));
+    const int bgrid = grid_for((const void*)motif_l3_block, 512, bsmem);
+    // per-warp scratch for I = A & B in the block kernel: |I| <= |A| <= dmax
+    P.scratch_stride = std::max<int64_t>(g.dmax, 1);
+    PGM_TRY(ws.scratch.reserve((size_t)bgrid * 16 * (size_t)P.scratch_stride));
+    P.scratch = ws.scratch.p;
+    const int64_t np = (int64_t)P.v_hi - P.v_lo;
+    int wgrid = grid_for((const void*)motif_l3_warp, threads, wsmem);
+    const int64_t blocks_needed = ((np + kMGrab - 1) / kMGrab + threads / 32 - 1) / (threads / 32);
+    wgrid = (int)std::max<int64_t>(1, std::min<int64_t>(wgrid, blocks_needed));
+    Profiler& prof = profiler();
+    int id = prof.begin("extend_sum", 3);
+    motif_l3_warp<<<wgrid, threads, wsmem, s>>>(P);
+    PGM_CHECK_LAUNCH();
+    motif_l3_block<<<bgrid, 512, bsmem, s>>>(P);
+    PGM_CHECK_LAUNCH();
+    prof.end(id, entries, 0.0);
+    return PGM_OK;
+  }
+
+  pgm_status prepare() {
+    PGM_TRY(graph_prepare_motifs(g));
+    PGM_TRY(ws.big.reserve((size_t)g.n / 2 + 2));  // every vertex fits (as int32)
+    PGM_TRY(ws.ctr.reserve(kNSlots));
+    PGM_TRY_CUDA(cudaMemsetAsync(ctr(), 0, kNSlots * sizeof(unsigned long long), s));
+    return PGM_OK;
+  }
+
+  pgm_status run3(int32_t v_lo, int32_t v_hi) { return launch_l2<mSum>(args(v_lo, v_hi), "extend_sum"); }
+
+  pgm_status run4(int32_t v_lo, int32_t v_hi) {
+    const int64_t a_lo = g.h_rp[v_lo], a_hi = g.h_rp[v_hi];
+    const int64_t E = a_hi - a_lo;  // arcs; arcs to lower neighbours get zero children
+    if (E == 0) return PGM_OK;
+    PGM_TRY(ws.cnt[2].reserve((size_t)E));
+    PGM_TRY(ws.off[2].reserve((size_t)E + 1));
+    PGM_TRY_CUDA(cudaMemsetAsync(ws.cnt[2].p, 0, (size_t)E * sizeof(uint32_t), s));
+    MotifArgs P = args(v_lo, v_hi);
+    P.cnt = ws.cnt[2].p;
+    PGM_TRY(launch_l2<mCount>(P, "extend_count"));
+    {
+      int id = profiler().begin("scan", 2);
+      PGM_TRY(exclusive_scan(ws.cnt[2].p, E, ws.off[2].p, ws, s));
+      profiler().end(id, (double)E, 12.0 * (double)E);
+    }
+    int64_t T = 0;
+    PGM_TRY(read_dev(ws.off[2].p + E, &T, s));
+    if (T == 0) return PGM_OK;
+    l3_size += (double)T;
+    const int64_t Bud = o.level_budget;
+    int32_t pa = v_lo;
+    while (pa < v_hi) {
+      int64_t base;
+      PGM_TRY(read_dev(ws.off[2].p + (g.h_rp[pa] - a_lo), &base, s));
+      int32_t pb;
+      if (T - base <= Bud) {
+        pb = v_hi;
+      } else {
+        int32_t lo = pa + 1, hi = v_hi;
+        pb = pa + 1;
+        while (lo <= hi) {
+          int32_t mid = lo + (hi - lo) / 2;
+          int64_t om;
+          PGM_TRY(read_dev(ws.off[2].p + (g.h_rp[mid] - a_lo), &om, s));
+          if (om - base <= Bud) {
+            pb = mid;
+            lo = mid + 1;
+          } else {
+            hi = mid - 1;
+          }
+        }
+      }
+      int64_t ob;
+      PGM_TRY(read_dev(ws.off[2].p + (g.h_rp[pb] - a_lo), &ob, s));
+      const int64_t Tp = ob - base;
+      chunks++;
+      if (Tp > 0) {
+        PGM_TRY(ws.vid[3].reserve((size_t)Tp));
+        MotifArgs W = args(pa, pb);
+        W.a_base = a_lo;
+        W.off = ws.off[2].p;
+        W.off_shift = base;
+        W.l3 = reinterpret_cast<uint32_t*>(ws.vid[3].p);
+        PGM_TRY(launch_l2<mWrite>(W, "extend_write"));
+        PGM_TRY(launch_l3(W, (double)Tp));
+      }
+      pa = pb;
+    }
+    return PGM_OK;
+  }
+};
+
+}  // namespace
+
+pgm_status count_motifs(Graph& g, Workspace& ws, cudaStream_t s, int k, int32_t v_lo, int32_t v_hi,
+                        uint64_t* out, unsigned long long* per_graph_dev) {
+  if (k != 3 && k != 4) {
+    set_error("count_motifs: k=%d unsupported (3 or 4)", k);
+    return PGM_EUNSUPPORTED;
+  }
+  if (v_lo < 0 || v_hi > g.n || v_lo > v_hi) {
+    set_error("count_motifs: bad vertex range [%d, %d)", v_lo, v_hi);
+    return PGM_EINVAL;
+  }
+  if (g.n >= (1 << 30)) {
+    set_error("count_motifs: n=%d needs 30-bit vertex IDs", g.n);
+    return PGM_EUNSUPPORTED;
+  }
+  MotifRun run(g, ws, s, k);
+  run.per_graph = per_graph_dev;
+  PGM_TRY(run.prepare());
+  if (v_hi > v_lo) {
+    if (k == 3)
+      PGM_TRY(run.run3(v_lo, v_hi));
+    else
+      PGM_TRY(run.run4(v_lo, v_hi));
+  }
+  unsigned long long h[kNSlots];
+  bool deferred = false;
+  PGM_TRY(read_counters(ws.ctr.p, h, kNSlots, s, &deferred));
+  if (deferred) return PGM_OK;  // replay: the caller reads the counters after the graph runs
+  if (h[kErr]) {
+    set_error("count_motifs: internal hub-list overflow");
+    return PGM_ENOMEM;
+  }
+  const int np = k == 3 ? 2 : 6;
+  for (int i = 0; i < np; i++) out[i] = h[kAcc + i];
+  pgm_profile& lp = last_profile();
+  Profiler& prof = profiler();
+  if (prof.on) {
+    PGM_TRY(prof.finish(&lp));
+    for (int i = 0; i < lp.nphases; i++) {
+      pgm_phase& p = lp.phase[i];
+      const int mode = !strcmp(p.name, "extend_count")   ? 0
+                       : !strcmp(p.name, "extend_write") ? 1
+                       : !strcmp(p.name, "extend_sum")   ? (k == 3 ? 2 : 3)
+                                                         : -1;
+      if (mode < 0) continue;
+      // neighbour-list elements read (4 B) + per-entry records (vid, row pointers: 12 B)
+      p.alg_bytes = 4.0 * (double)h[kStat + mode] + 12.0 * p.entries;
+    }
+  }
+  const int64_t m = (g.h_rp[v_hi] - g.h_rp[v_lo]) / 2;
+  lp.level_size[1] = (uint64_t)(v_hi - v_lo);
+  lp.level_size[2] = (uint64_t)m;
+  if (k == 3) {
+    lp.level_size[3] = out[0] + out[1];
+  } else {
+    lp.level_size[3] = (uint64_t)run.l3_size;
+    uint64_t t = 0;
+    for (int i = 0; i < 6; i++) t += out[i];
+    lp.level_size[4] = t;
+  }
+  lp.chunks = run.chunks;
+  return PGM_OK;
+}
+
+}  // namespace pgm
+
+extern "C" {
+
+pgm_status pgm_count_motifs(pgm_graph* g, int32_t k, uint64_t* out_counts, int32_t cap) {
+  if (!g || !out_counts) {
+    pgm::set_error("pgm_count_motifs: null argument");
+    return PGM_EINVAL;
+  }
+  if (k == 3 || k == 4) {
+    if ((k == 3 && cap < 2) || (k == 4 && cap < 6)) {
+      pgm::set_error("pgm_count_motifs: output capacity %d too small for k=%d", cap, k);
+      return PGM_EINVAL;
+    }
+  }
+  pgm::profiler().start(g->g.stream);
+  uint64_t c[6] = {0, 0, 0, 0, 0, 0};
+  PGM_TRY(pgm::count_motifs(g->g, g->g.ws, g->g.stream, k, 0, g->g.n, c, nullptr));
+  memcpy(out_counts, c, sizeof(uint64_t) * (k == 3 ? 2 : 6));
+  return PGM_OK;
+}
+
+pgm_status pgm_count_motifs_range(pgm_graph* g, int32_t k, int32_t v_lo, int32_t v_hi,
+                                  uint64_t* out_counts, int32_t cap) {
+  if (!g || !out_counts) {
+    pgm::set_error("pgm_count_motifs_range: null argument");
+    return PGM_EINVAL;
+  }
+  if ((k == 3 && cap < 2) || (k == 4 && cap < 6)) {
+    pgm::set_error("pgm_count_motifs_range: output capacity too small");
+    return PGM_EINVAL;
+  }
+  pgm::profiler().start(g->g.stream);
+  uint64_t c[6] = {0, 0, 0, 0, 0, 0};
+  PGM_TRY(pgm::count_motifs(g->g, g->g.ws, g->g.stream, k, v_lo, v_hi, c, nullptr));
+  memcpy(out_counts, c, sizeof(uint64_t) * (k == 3 ? 2 : 6));
+  return PGM_OK;
+}
+
+}  // extern "C"
