@@ -1,0 +1,367 @@
+"""Benchmark: exact 4-clique counting on R-MAT scale 21 (28,000,000 edges).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--no-extras]
+
+A step is one pgm_count_kcliques(g, 4) call on the device-resident, oriented
+graph: level 2 (the DAG) -> inspection -> scan -> level 3 (triangles, written)
+-> fused level-4 count.  The metric is embeddings per second: the embeddings
+of every level the step enumerates, |L2| + |L3| + |L4| (edges + triangles +
+4-cliques), divided by the step time.  L2 is flushed (a 256 MiB device write)
+between timed steps, outside the timed events.
+
+Under torchrun (N > 1) each rank counts the part of the 4-cliques whose
+first DAG vertex lies in its share of the vertices (shares balanced by
+sum of squared out-degrees) and the counts are summed at the end (strong
+scaling: the total work is fixed).
+
+Extras (N = 1, rank 0; --no-extras skips them): 4-motif counting on the
+Chung-Lu graph (1M vertices, exponent 2.1), and the batched path (20,000
+small graphs in one pass, replayed as a CUDA graph) against the per-graph
+launch loop.
+
+--impl reference times the CPU oracle (as it stands, on all host cores) on a
+bounded sample of the same workload, in the same metric.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import graphgen as gg  # noqa: E402
+
+METRIC = "embeddings/s and wall time for 4-clique & 4-motif (exact); batched vs plain speedup"
+WORKLOAD = "4-clique count, R-MAT scale 21 (a,b,c,d)=(0.57,0.19,0.19,0.05), 28,000,000 undirected edges, degree-oriented DAG"
+GOLD = os.path.join(ROOT, "tests", "golden")
+
+
+def load_json(path):
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return None
+
+
+def peaks():
+    d = load_json(os.path.join(ROOT, "MEASURED_PEAKS.json"))
+    if d and d.get("hbm_gbs"):
+        return float(d["hbm_gbs"]), "measured"
+    return 6400.0, "fallback"
+
+
+# --------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, dev: int):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                       "-lms", "200", "-i", str(dev)], stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self) -> dict:
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.p.terminate()
+        self.p.wait()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[0]))
+                mx.append(float(r[1]))
+                for nm, v in zip(names, r[3:7]):
+                    if v.strip().lower() in ("active", "1"):
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------ partition
+def vertex_shares(g, world):
+    """Contiguous vertex ranges with about equal sum of squared DAG out-degrees."""
+    if world == 1:
+        return [(0, g.n)]
+    deg = np.diff(g.rowptr)
+    src = np.repeat(np.arange(g.n, dtype=np.int64), deg)
+    dc = deg[g.col]
+    ds = deg[src]
+    keep = (ds < dc) | ((ds == dc) & (src < g.col))
+    outdeg = np.bincount(src[keep], minlength=g.n).astype(np.float64)
+    c = np.cumsum(outdeg * outdeg + 1.0)
+    cuts = [0] + [int(np.searchsorted(c, c[-1] * r / world)) for r in range(1, world)] + [g.n]
+    return list(zip(cuts[:-1], cuts[1:]))
+
+
+# ----------------------------------------------------------- oracle legs
+def oracle_sample(g, k, target_s=12.0):
+    """Time the oracle clique enumerator on a bounded root sample; embeddings/s."""
+    import oracle
+
+    threads = os.cpu_count() or 1
+    r = max(1, g.n // 512)
+    t0 = time.perf_counter()
+    lv = oracle.clique_levels(g, k, "degree", roots=(0, r), threads=threads)
+    t1 = time.perf_counter() - t0
+    if t1 < target_s / 4:
+        r = min(g.n, int(r * target_s / max(t1, 1e-3)))
+        t0 = time.perf_counter()
+        lv = oracle.clique_levels(g, k, "degree", roots=(0, r), threads=threads)
+        t1 = time.perf_counter() - t0
+    emb = sum(lv[2:k + 1])
+    return {"value": emb / t1, "unit": "embeddings/s", "cores": threads, "kind": "oracle",
+            "sample": f"orc_clique_count (degree order, OpenMP) on roots [0, {r}) of {g.n} vertices "
+                      f"({emb} embeddings of levels 2..{k}) in {t1:.2f} s"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    g = gg.rmat21()
+    cb = oracle_sample(g, 4)
+    steps = []
+    for _ in range(args.warmup + args.steps):
+        steps.append(oracle_sample(g, 4, target_s=max(2.0, 60.0 / (args.warmup + args.steps))))
+    timed = steps[args.warmup:]
+    v = float(np.mean([s["value"] for s in timed]))
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "embeddings/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
+            "scaling": "strong", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": timed[-1]["sample"]},
+            "cpu_baseline": {**cb, "value": v},
+            "e2e": {"value": v, "unit": "embeddings/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------- our arm
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+
+    from paper_1911_06969_b300 import pgm
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def allreduce(x, op):
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=op)
+        return float(t.item())
+
+    g = gg.rmat21()
+    lo, hi = vertex_shares(g, world)[rank]
+    stream = torch.cuda.Stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    G = pgm.Graph(g, stream=stream)
+    G.orient()
+    pgm.pgm_set_options(profile=1)
+
+    def step():
+        return pgm.pgm_count_kcliques_range(G.h, 4, lo, hi)
+
+    for _ in range(args.warmup):
+        count = step()
+    prof = pgm.pgm_last_profile()
+    emb = sum(prof["level_size"][2:5])  # |L2| + |L3| + |L4| of this rank's share
+
+    clocks = ClockSampler(local)
+    barrier()
+    torch.cuda.synchronize()
+    launches0 = pgm.pgm_kernel_launches()
+    ms, dom_ms, dom_bytes, dom_launches = [], 0.0, 0.0, 0
+    for _ in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(1)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        c = step()
+        e1.record(stream)
+        e1.synchronize()
+        assert c == count, "count changed between steps"
+        ms.append(e0.elapsed_time(e1))
+        for ph in pgm.pgm_last_profile()["phases"]:
+            if ph["name"] == "extend_sum":
+                dom_ms += ph["ms"]
+                dom_bytes += ph["alg_bytes"]
+                dom_launches += ph["launches"]
+    torch.cuda.synchronize()
+    barrier()
+    launches = pgm.pgm_kernel_launches() - launches0
+    clk = clocks.stop()
+    total_ms = allreduce(sum(ms), dist.ReduceOp.MAX if world > 1 else None)
+    total_emb = allreduce(float(emb), dist.ReduceOp.SUM if world > 1 else None)
+    total_count = int(allreduce(float(count), dist.ReduceOp.SUM if world > 1 else None))
+    pgm.pgm_set_options(profile=0)
+
+    if rank != 0:
+        G.close()
+        if world > 1:
+            dist.destroy_process_group()
+        return 0
+
+    value = total_emb * args.steps / (total_ms * 1e-3)
+    gold = load_json(os.path.join(GOLD, "rmat21.json"))
+    exact = None
+    if gold and world == 1:
+        exact = gold["clique_levels_k4"][4] == total_count
+    hbm, peak_kind = peaks()
+    achieved = dom_bytes / (dom_ms * 1e-3) / 1e9 if dom_ms > 0 else None
+    traffic_rec = load_json(os.path.join(ROOT, "profiles", "traffic.json")) or {}
+    traffic = traffic_rec.get("extend_sum_rmat21_k4")
+    line = {
+        "metric": METRIC, "value": value, "unit": "embeddings/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "strong", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": g.n, "m": g.m, "k": 4, "l2_flush": "256 MiB device write between steps",
+                   "embeddings_per_step": total_emb, "count": total_count, "exact_vs_oracle": exact,
+                   "step_ms": [round(x, 3) for x in ms]},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": achieved / hbm if achieved else None, "traffic": traffic,
+                     "kernel": "extend_sum level 3 (clique_warp_kernel<kSum> + clique_block_kernel<kSum>)",
+                     "kernel_ms_per_launch": dom_ms / max(dom_launches, 1),
+                     "alg_bytes_per_launch": dom_bytes / max(dom_launches, 1), "peak_kind": peak_kind},
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    # end to end through the C ABI from pinned host buffers
+    line["e2e"] = e2e(g, pgm, torch, stream, emb)
+    if not args.no_cpu_baseline and world == 1:
+        line["cpu_baseline"] = oracle_sample(g, 4)
+    G.close()
+    if not args.no_extras and world == 1:
+        line["extras"] = extras(pgm, torch, stream, flush)
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def e2e(g, pgm, torch, stream, emb, steps=2):
+    rp = torch.from_numpy(g.rowptr).pin_memory()
+    col = torch.from_numpy(g.col).pin_memory()
+    rpn, coln = rp.numpy(), col.numpy()
+    ts = []
+    for i in range(steps + 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        h = pgm.pgm_graph_create_csr(g.n, rpn, coln, 0, stream)
+        try:
+            c = pgm.pgm_count_kcliques(h, 4)
+        finally:
+            pgm.pgm_graph_destroy(h)
+        t1 = time.perf_counter()
+        if i > 0:
+            ts.append(t1 - t0)
+    t = float(np.mean(ts))
+    return {"value": emb / t, "unit": "embeddings/s", "h2d_bytes_per_step": (g.n + 1) * 4 + g.narcs * 4,
+            "d2h_bytes_per_step": (g.n + 1) * 8 + 96 * 8 + 16, "ms_per_step": t * 1e3, "count": c,
+            "includes": "graph upload from pinned host CSR, orientation, count, result readback"}
+
+
+def extras(pgm, torch, stream, flush):
+    out = {}
+    # 4-motif counting on the Chung-Lu graph
+    g = gg.chung_lu_1m()
+    gold = load_json(os.path.join(GOLD, "chung_lu_1m.json"))
+    pgm.pgm_set_options(profile=1)
+    with pgm.Graph(g, stream=stream) as G:
+        G.motifs(4)
+        ms, dom_ms, dom_b = [], 0.0, 0.0
+        for _ in range(2):
+            with torch.cuda.stream(stream):
+                flush.fill_(2)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            m4 = G.motifs(4)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            p = pgm.pgm_last_profile()
+            for ph in p["phases"]:
+                if ph["name"] == "extend_sum":
+                    dom_ms += ph["ms"]
+                    dom_b += ph["alg_bytes"]
+        emb = sum(p["level_size"][2:5])
+    pgm.pgm_set_options(profile=0)
+    t = float(np.mean(ms))
+    out["motif4_chung_lu_1m"] = {
+        "value": emb / (t * 1e-3), "unit": "embeddings/s", "ms_per_step": t, "counts": m4,
+        "exact_vs_oracle": (gold["motif4"] == m4) if gold else None, "embeddings_per_step": emb,
+        "last_level_alg_GBps": dom_b / (dom_ms * 1e-3) / 1e9 if dom_ms else None}
+    # batched many-small-graphs path vs the per-graph loop
+    b = gg.small_batch_20k()
+    gold = load_json(os.path.join(GOLD, "small_batch_20k.json"))
+    h = pgm.pgm_batch_create(b.G, b.vtx_off, b.graph.rowptr, b.graph.col)
+    try:
+        tune, tune_ms = pgm.pgm_batch_autotune(h, 4)
+        x = pgm.pgm_batch_count_motifs(h, 4, tune)  # capture
+        tb = []
+        for _ in range(3):
+            t0 = time.perf_counter()
+            x = pgm.pgm_batch_count_motifs(h, 4, tune)
+            tb.append(time.perf_counter() - t0)
+        t0 = time.perf_counter()
+        y = pgm.pgm_batch_count_motifs_loop(h, 4)
+        tl = time.perf_counter() - t0
+        import hashlib
+
+        digest = hashlib.sha256(np.ascontiguousarray(x, np.uint64).tobytes()).hexdigest()
+        out["batched_small_graphs_20k"] = {
+            "graphs": b.G, "batched_ms": float(np.mean(tb)) * 1e3, "loop_ms": tl * 1e3,
+            "speedup": tl / float(np.mean(tb)), "tune": tune.as_dict(), "autotune_best_ms": tune_ms,
+            "identical_counts": bool((x == y).all()),
+            "exact_vs_oracle": (digest == gold["motif4_sha256"]) if gold else None}
+    finally:
+        pgm.pgm_batch_destroy(h)
+    return out
+
+
+if __name__ == "__main__":
+    sys.exit(main())

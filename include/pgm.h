@@ -172,6 +172,8 @@ pgm_status pgm_count_motifs_range(pgm_graph *g, int32_t k, int32_t v_lo, int32_t
  *   vtx_off     int64[G+1], vtx_off[0] = 0, non-decreasing
  *   rowptr_cat  int64[vtx_off[G]+1]
  *   col_cat     int32[rowptr_cat[vtx_off[G]]]
+ * A NULL stream makes the batch create (and own) a non-blocking stream,
+ * since CUDA-graph capture needs a stream other than the legacy default.
  * (not in the paper: many-small-graphs batching). */
 pgm_status pgm_batch_create(int32_t G, const int64_t *vtx_off, const int64_t *rowptr_cat,
                             const int32_t *col_cat, uint32_t flags, void *stream, pgm_batch **out);
@@ -261,6 +263,9 @@ pgm_status pgm_exclusive_scan_dev(const uint32_t *cnt_dev, int64_t len, int64_t 
                                   void *stream);
 const char *pgm_last_error(void);
 const char *pgm_version(void);
+/* Number of CUDA kernels this library has launched in the process (all
+ * threads; a CUDA-graph replay adds the kernel nodes of the graph). */
+uint64_t pgm_kernel_launches(void);
 
 #ifdef __cplusplus
 }

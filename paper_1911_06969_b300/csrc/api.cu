@@ -2,6 +2,7 @@
 // queries, the launch profiler, record/replay plans and the small C-ABI
 // entry points.
 #include <algorithm>
+#include <atomic>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -24,6 +25,9 @@ void set_error(const char* fmt, ...) {
 }
 
 const char* get_error() { return t_err.c_str(); }
+
+static std::atomic<uint64_t> g_launches{0};
+void note_launches(uint64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 static pgm_options g_opts = {256, 512, 0, 0, (int64_t)1 << 29, 0, {0}};
 
@@ -216,6 +220,8 @@ extern "C" {
 const char* pgm_last_error(void) { return pgm::get_error(); }
 
 const char* pgm_version(void) { return "libpgm 0.2 (sm_103a)"; }
+
+uint64_t pgm_kernel_launches(void) { return pgm::g_launches.load(std::memory_order_relaxed); }
 
 pgm_status pgm_set_options(const pgm_options* o) {
   if (!o) {

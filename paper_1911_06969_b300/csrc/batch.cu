@@ -68,10 +68,12 @@ struct pgm_batch {
   pgm::DevArr<unsigned long long> per_graph;  // G * 6
   unsigned long long* pinned_pg = nullptr;    // host-pinned copy of per_graph
   unsigned long long* pinned_ctr = nullptr;   // host-pinned counter block
+  cudaStream_t own_stream = nullptr;          // created when the caller passes NULL
   struct Cap {
     int kind, k;
     pgm_tune t;
     cudaGraphExec_t exec = nullptr;
+    uint64_t kernel_nodes = 0;
     std::unique_ptr<pgm::Workspace> ws;
   };
   std::vector<std::unique_ptr<Cap>> caps;
@@ -225,6 +227,17 @@ pgm_status run_batch(pgm_batch* b, int kind, int k, uint64_t* out, const pgm_tun
       set_error("batch: replay consumed %zu of %zu recorded reads", plan.cur, plan.v.size());
       return PGM_EINVAL;
     }
+    size_t nn = 0;
+    if (cudaGraphGetNodes(graph, nullptr, &nn) == cudaSuccess && nn > 0) {
+      std::vector<cudaGraphNode_t> nodes(nn);
+      if (cudaGraphGetNodes(graph, nodes.data(), &nn) == cudaSuccess)
+        for (size_t i = 0; i < nn; i++) {
+          cudaGraphNodeType ty;
+          if (cudaGraphNodeGetType(nodes[i], &ty) == cudaSuccess && ty == cudaGraphNodeTypeKernel)
+            c->kernel_nodes++;
+        }
+    }
+    cudaGetLastError();
     cudaError_t ie = cudaGraphInstantiate(&c->exec, graph, 0);
     cudaGraphDestroy(graph);
     if (ie != cudaSuccess) {
@@ -236,6 +249,7 @@ pgm_status run_batch(pgm_batch* b, int kind, int k, uint64_t* out, const pgm_tun
     b->caps.push_back(std::move(c));
   }
   PGM_TRY_CUDA(cudaGraphLaunch(cap->exec, s));
+  note_launches(cap->kernel_nodes);
   PGM_TRY_CUDA(cudaStreamSynchronize(s));
   PGM_TRY(check_err_slots(b->pinned_ctr, kind));
   memcpy(out, b->pinned_pg, pg_bytes);
@@ -275,6 +289,15 @@ pgm_status pgm_batch_create(int32_t G, const int64_t* vtx_off, const int64_t* ro
     return st;
   };
   cudaStream_t s = (cudaStream_t)stream;
+  if (!s) {
+    // the legacy default stream cannot be captured into a CUDA graph
+    if (cudaStreamCreateWithFlags(&b->own_stream, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      pgm::set_error("pgm_batch_create: stream creation failed");
+      return fail(PGM_ECUDA);
+    }
+    s = b->own_stream;
+  }
   pgm::profiler().start(s);
   pgm_status st = pgm::graph_upload(b->g, (int32_t)n, rowptr_cat, col_cat, false, 0,
                                     flags & ~PGM_SANITIZE, s);
@@ -454,6 +477,7 @@ void pgm_batch_destroy(pgm_batch* b) {
   if (b->pinned_pg) cudaFreeHost(b->pinned_pg);
   if (b->pinned_ctr) cudaFreeHost(b->pinned_ctr);
   pgm::graph_free(b->g);
+  if (b->own_stream) cudaStreamDestroy(b->own_stream);
   delete b;
 }
 

@@ -36,7 +36,14 @@ const char* get_error();
     if (s_ != PGM_OK) return s_; \
   } while (0)
 
-#define PGM_CHECK_LAUNCH() PGM_TRY_CUDA(cudaGetLastError())
+// every kernel launch of the library is followed by this check, which also
+// counts it (pgm_kernel_launches)
+void note_launches(uint64_t n);
+#define PGM_CHECK_LAUNCH()              \
+  do {                                  \
+    ::pgm::note_launches(1);            \
+    PGM_TRY_CUDA(cudaGetLastError());   \
+  } while (0)
 
 // ----------------------------------------------------------------- options
 pgm_options& options();  // current options (defaults filled); read-only while counting

@@ -115,6 +115,7 @@ _SIGS = {
     "pgm_exclusive_scan_dev": (C.c_int, [P, C.c_int64, P, P]),
     "pgm_last_error": (C.c_char_p, []),
     "pgm_version": (C.c_char_p, []),
+    "pgm_kernel_launches": (C.c_uint64, []),
 }
 
 _lib = None
@@ -339,6 +340,10 @@ def pgm_last_error() -> str:
 
 def pgm_version() -> str:
     return load().pgm_version().decode()
+
+
+def pgm_kernel_launches() -> int:
+    return int(load().pgm_kernel_launches())
 
 
 # -------------------------------------------------------------- convenience
