@@ -56,6 +56,7 @@ struct LevelArgs {
   int hub;                    // segment length above which a parent is a hub
   int cap;                    // per-warp staging capacity (ints)
   int block_cap;              // per-block staging capacity (ints)
+  int rev_ratio;              // reverse scan when d+(w) > rev_ratio * |segment|
   const int32_t* gid;         // vertex -> graph (batches) or nullptr
   unsigned long long* per_graph;  // kSum with gid: per-graph counts
 };
@@ -74,20 +75,26 @@ __device__ __forceinline__ void flush_count(const LevelArgs& A, unsigned long lo
 }
 
 // Process entries j0 .. j0+31 of a staged segment S (length s).  e0 is the
-// output index of S[0].  Children of entry j are N+(S[j]) & S.
+// output index of S[0].  Children of entry j are N+(S[j]) & S, found either
+// forward (scan N+(w), binary-search S in shared memory) or in reverse when
+// N+(w) is much longer than S (scan S, binary-search N+(w)); both visit the
+// children in ascending ID order.
 template <int MODE>
 __device__ __forceinline__ void process_batch(const int32_t* S, int s, int j0, int64_t e0,
                                               const LevelArgs& A, int lane, uint32_t* wcnt,
                                               unsigned long long& tot, unsigned long long& lensum) {
   const int j = j0 + lane;
   const bool valid = j < s;
-  int32_t a0 = 0, len = 0;
+  int32_t a0 = 0, d = 0, len = 0;
+  int rev = 0;
   if (valid) {
     const int32_t w = S[j];
     a0 = A.rp[w];
-    len = A.rp[w + 1] - a0;
+    d = A.rp[w + 1] - a0;
+    rev = d > A.rev_ratio * s;
+    len = rev ? s : d;
   }
-  lensum += (unsigned long long)len;
+  lensum += (unsigned long long)d;
   const int incl = warp_inclusive_scan(len, lane);
   const int total = __shfl_sync(kFull, incl, 31);
   const int excl = incl - len;
@@ -104,11 +111,18 @@ __device__ __forceinline__ void process_batch(const int32_t* S, int s, int j0, i
     const int q = min(warp_owner(incl, t), 31);
     const int aq = __shfl_sync(kFull, a0, q);
     const int eq = __shfl_sync(kFull, excl, q);
+    const int revq = __shfl_sync(kFull, rev, q);
+    const int dq = __shfl_sync(kFull, d, q);
     bool hit = false;
     int32_t x = 0;
     if (active) {
-      x = A.col[aq + (t - eq)];
-      hit = x >= smin && x <= smax && contains_dev(S, s, x);
+      if (!revq) {
+        x = A.col[aq + (t - eq)];
+        hit = x >= smin && x <= smax && contains_dev(S, s, x);
+      } else {
+        x = S[t - eq];
+        hit = contains_dev(A.col + aq, dq, x);
+      }
     }
     if (MODE == kSum) {
       tot += hit ? 1ull : 0ull;
@@ -321,6 +335,7 @@ struct CliqueRun {
     A.hub = hub;
     A.cap = cap;
     A.block_cap = block_cap;
+    A.rev_ratio = 4;
     A.gid = g.gid;
     A.per_graph = per_graph;
     const int threads = o.block_threads;

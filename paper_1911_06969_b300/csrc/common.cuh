@@ -128,6 +128,11 @@ struct Graph {
   int32_t* dag_col = nullptr;  // int32[m]
   int32_t* up = nullptr;       // up[v] = first arc of v whose neighbour is > v
   int32_t* gid = nullptr;      // batches: vertex -> graph id (nullptr otherwise)
+  int32_t* src = nullptr;      // motifs: source vertex of every arc
+  int32_t* hub_idx = nullptr;  // motifs: vertex -> row of hub_bits, or -1
+  uint32_t* hub_bits = nullptr;  // motifs: adjacency bitmaps of the highest-degree vertices
+  int64_t hub_words = 0;       // 32-bit words per bitmap row
+  int32_t nhubs = 0;
   int32_t G = 1;
   int64_t dmax = 0, dag_dmax = 0;
   bool oriented = false;

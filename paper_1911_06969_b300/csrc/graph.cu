@@ -97,6 +97,28 @@ __global__ void upper_kernel(int32_t n, const int32_t* __restrict__ rp, const in
   }
 }
 
+// src[a] = v for every arc a of v
+__global__ void src_kernel(int32_t n, const int32_t* __restrict__ rp, int32_t* __restrict__ src) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t v = warp; v < n; v += nwarps)
+    for (int32_t a = rp[v] + lane; a < rp[v + 1]; a += 32) src[a] = (int32_t)v;
+}
+
+// one block per hub: set the bits of its neighbours in its bitmap row
+__global__ void hub_bits_kernel(const int32_t* __restrict__ hubs, int32_t nh, const int32_t* __restrict__ rp,
+                                const int32_t* __restrict__ col, uint32_t* __restrict__ bits, int64_t words) {
+  for (int32_t h = blockIdx.x; h < nh; h += gridDim.x) {
+    const int32_t v = hubs[h];
+    uint32_t* row = bits + (int64_t)h * words;
+    for (int32_t a = rp[v] + threadIdx.x; a < rp[v + 1]; a += blockDim.x) {
+      const int32_t w = col[a];
+      atomicOr(row + (w >> 5), 1u << (w & 31));
+    }
+  }
+}
+
 static int warp_grid(int64_t items, int threads) {
   int64_t blocks = (items * 32 + threads - 1) / threads;
   int64_t cap = (int64_t)num_sms() * 16;
@@ -134,7 +156,12 @@ void graph_free(Graph& g) {
   if (g.dag_col) cudaFree(g.dag_col);
   if (g.gid) cudaFree(g.gid);
   if (g.up) cudaFree(g.up);
-  g.rp = g.col = g.dag_rp = g.dag_col = g.gid = g.up = nullptr;
+  if (g.src) cudaFree(g.src);
+  if (g.hub_idx) cudaFree(g.hub_idx);
+  if (g.hub_bits) cudaFree(g.hub_bits);
+  g.rp = g.col = g.dag_rp = g.dag_col = g.gid = g.up = g.src = g.hub_idx = nullptr;
+  g.hub_bits = nullptr;
+  g.nhubs = 0;
   g.ws.release_all();
   g.oriented = false;
 }
@@ -278,15 +305,58 @@ pgm_status graph_orient(Graph& g) {
   return PGM_OK;
 }
 
+// Motif helpers, built once per graph: up[] (first arc to a larger ID),
+// src[] (source vertex of each arc) and adjacency bitmaps of the vertices
+// of degree >= kHubDegree (highest degrees first, at most kHubBytes), used
+// for O(1) membership tests against hub adjacency lists.
+constexpr int64_t kHubDegree = 1024;
+constexpr int64_t kHubBytes = (int64_t)512 << 20;
+
 pgm_status graph_prepare_motifs(Graph& g) {
   if (g.up) return PGM_OK;
-  PGM_TRY_CUDA(cudaMalloc(&g.up, ((size_t)g.n + 1) * sizeof(int32_t)));
-  if (g.n > 0) {
-    const int blocks = std::max(1, std::min(num_sms() * 8, (g.n + 255) / 256));
-    upper_kernel<<<blocks, 256, 0, g.stream>>>(g.n, g.rp, g.col, g.up);
+  cudaStream_t s = g.stream;
+  const int32_t n = g.n;
+  PGM_TRY_CUDA(cudaMalloc(&g.up, ((size_t)n + 1) * sizeof(int32_t)));
+  PGM_TRY_CUDA(cudaMalloc(&g.src, (size_t)std::max<int64_t>(g.narcs, 1) * sizeof(int32_t)));
+  PGM_TRY_CUDA(cudaMalloc(&g.hub_idx, ((size_t)n + 1) * sizeof(int32_t)));
+  PGM_TRY_CUDA(cudaMemsetAsync(g.hub_idx, 0xff, ((size_t)n + 1) * sizeof(int32_t), s));
+  if (n > 0) {
+    const int blocks = std::max(1, std::min(num_sms() * 8, (n + 255) / 256));
+    upper_kernel<<<blocks, 256, 0, s>>>(n, g.rp, g.col, g.up);
+    PGM_CHECK_LAUNCH();
+    src_kernel<<<warp_grid(n, 256), 256, 0, s>>>(n, g.rp, g.src);
     PGM_CHECK_LAUNCH();
   }
-  PGM_TRY_CUDA(cudaStreamSynchronize(g.stream));
+  // hubs: highest degrees first
+  std::vector<std::pair<int64_t, int32_t>> cand;
+  for (int32_t v = 0; v < n; v++) {
+    const int64_t d = g.h_rp[v + 1] - g.h_rp[v];
+    if (d >= kHubDegree) cand.push_back({-d, v});
+  }
+  std::sort(cand.begin(), cand.end());
+  g.hub_words = ((int64_t)n + 31) / 32;
+  int64_t maxh = g.hub_words > 0 ? kHubBytes / (g.hub_words * 4) : 0;
+  const int32_t nh = (int32_t)std::min<int64_t>((int64_t)cand.size(), maxh);
+  if (nh > 0) {
+    std::vector<int32_t> hubs(nh), idx(nh);
+    for (int32_t h = 0; h < nh; h++) hubs[h] = cand[h].second;
+    PGM_TRY_CUDA(cudaMalloc(&g.hub_bits, (size_t)nh * g.hub_words * sizeof(uint32_t)));
+    PGM_TRY_CUDA(cudaMemsetAsync(g.hub_bits, 0, (size_t)nh * g.hub_words * sizeof(uint32_t), s));
+    int32_t* d_hubs = nullptr;
+    PGM_TRY_CUDA(cudaMalloc(&d_hubs, (size_t)nh * sizeof(int32_t)));
+    PGM_TRY_CUDA(cudaMemcpyAsync(d_hubs, hubs.data(), (size_t)nh * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    hub_bits_kernel<<<std::min(nh, num_sms() * 4), 256, 0, s>>>(d_hubs, nh, g.rp, g.col, g.hub_bits,
+                                                                g.hub_words);
+    PGM_CHECK_LAUNCH();
+    for (int32_t h = 0; h < nh; h++) idx[h] = h;
+    // scatter the row numbers into hub_idx (one small copy per hub)
+    for (int32_t h = 0; h < nh; h++)
+      PGM_TRY_CUDA(cudaMemcpyAsync(g.hub_idx + hubs[h], &idx[h], sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    PGM_TRY_CUDA(cudaStreamSynchronize(s));
+    cudaFree(d_hubs);
+  }
+  g.nhubs = nh;
+  PGM_TRY_CUDA(cudaStreamSynchronize(s));
   return PGM_OK;
 }
 

@@ -43,6 +43,7 @@ namespace {
 
 enum MMode : int { mCount = 0, mWrite = 1, mSum = 2 };
 constexpr int kMGrab = 2;
+constexpr int kEdgeGrab = 4;
 constexpr uint32_t kVidMask = (1u << 30) - 1u;
 constexpr uint32_t kA02 = 1u << 30;
 constexpr uint32_t kA12 = 1u << 31;
@@ -85,8 +86,15 @@ struct MotifArgs {
   int64_t big_cap;
   int cap;        // per-warp staging capacity (ints) per list
   int block_cap;  // per-block staging capacity for A
-  int32_t* scratch;  // per-warp global scratch (block kernel), scratch_stride ints each
+  int32_t* scratch;  // per-warp global scratch, scratch_stride ints each
   int64_t scratch_stride;
+  // level 3
+  const int32_t* src;       // src[a] = source vertex of arc a
+  int64_t arc_lo, arc_hi;   // arcs of this chunk (absolute)
+  const int32_t* hub_idx;   // vertex -> hub bitmap row or -1
+  const uint32_t* hub_bits; // adjacency bitmaps of hub vertices
+  int64_t hub_words;        // words per bitmap row
+  int rev_ratio;            // reverse scan when d(v2) > rev_ratio * (|A| + |B|)
 };
 
 template <int N>
@@ -294,152 +302,70 @@ __global__ void __launch_bounds__(512) motif_l2_block(MotifArgs P) {
 }
 
 // ------------------------------------------------------------- level 3 (last)
-// One edge (v0, v1 = A[j]): B = N(v1) & (v0, inf), I = A & B, then the
-// children of the edge from the level-3 list.
-__device__ __forceinline__ void l3_edge(const MotifArgs& P, const int32_t* A, int s, int j,
-                                        int32_t v0, int64_t arc0, int lane, int32_t* Bbuf,
-                                        int32_t* Ibuf, long long (&c)[6],
-                                        unsigned long long& seen) {
-  const int32_t v1 = A[j];
-  const int64_t cb = P.off[arc0 + j] - P.off_shift;
-  const int64_t ce = P.off[arc0 + j + 1] - P.off_shift;
-  if (ce <= cb) return;
-  // B: suffix of N(v1) above v0
-  const int32_t r0 = P.rp[v1], r1 = P.rp[v1 + 1];
-  int bstart = 0;
-  if (lane == 0) bstart = lower_bound_dev(P.col + r0, r1 - r0, v0 + 1);
-  bstart = __shfl_sync(kFull, bstart, 0);
-  const int nb = r1 - r0 - bstart;
-  const int32_t* B;
-  if (nb <= P.cap) {
-    for (int i = lane; i < nb; i += 32) Bbuf[i] = P.col[r0 + bstart + i];
-    B = Bbuf;
-  } else {
-    B = P.col + r0 + bstart;
-  }
-  __syncwarp();
-  // I = A & B (sorted): iterate the shorter list, search the longer one
-  int ni = 0;
-  {
-    const bool iterA = s <= nb;
-    const int32_t* X = iterA ? A : B;
-    const int32_t* Y = iterA ? B : A;
-    const int nx = iterA ? s : nb, ny = iterA ? nb : s;
-    for (int i0 = 0; i0 < nx; i0 += 32) {
-      const int i = i0 + lane;
-      bool in = false;
-      int32_t x = 0;
-      if (i < nx) {
-        x = X[i];
-        in = contains_dev(Y, ny, x);
-      }
-      const unsigned b = __ballot_sync(kFull, in);
-      if (in) Ibuf[ni + __popc(b & ((1u << lane) - 1u))] = x;
-      ni += __popc(b);
+// Membership of w in a sorted list, or by one bit of a hub's adjacency
+// bitmap when the list's owner is a hub (hb >= 0).  Callers only ask about
+// w above the list's lower threshold, so the bitmap of the full adjacency
+// list answers for the thresholded list too.
+__device__ __forceinline__ bool member(const int32_t* L, int len, int hb, const MotifArgs& P, int32_t w) {
+  if (hb >= 0) return (P.hub_bits[(int64_t)hb * P.hub_words + (w >> 5)] >> (w & 31)) & 1u;
+  return len > 0 && w >= L[0] && w <= L[len - 1] && contains_dev(L, len, w);
+}
+
+// Contribution of one candidate w (adjacency bits a, b, c to v0, v1, v2) of
+// the 3-embedding with memo (a02, a12), given that w is adjacent to v2:
+// the canonical test accepts it (region thresholds of the header comment)
+// and its pattern is counted; the rank-based count of its (a, b) region,
+// which included it, is corrected.
+__device__ __forceinline__ void add_c_region(long long (&c)[6], int a02, int a12, int a, int b,
+                                             int32_t w, int32_t v2) {
+  const int M = 4 | a | (b << 1);
+  if (!a && !b) {
+    add_pat<6>(c, pattern4(a02, a12, 4), 1);
+  } else if (a02) {
+    if (!a || w > v2) {  // adjacent to v0: needs w > v2; to v1 only: always
+      add_pat<6>(c, pattern4(1, a12, M), 1);
+      add_pat<6>(c, pattern4(1, a12, M & 3), -1);
     }
-  }
-  __syncwarp();
-  if (lane == 0) seen += (unsigned long long)(nb + s);
-  const int32_t amin = A[0], amax = A[s - 1];
-  const int32_t bmin = nb > 0 ? B[0] : 0, bmax = nb > 0 ? B[nb - 1] : -1;
-  // children, 32 at a time
-  for (int64_t c0 = cb; c0 < ce; c0 += 32) {
-    const int64_t ci = c0 + lane;
-    const bool valid = ci < ce;
-    int32_t v2 = 0, a0 = 0, len = 0;
-    int a02 = 0, a12 = 0;
-    if (valid) {
-      const uint32_t e = P.l3[ci];
-      v2 = (int32_t)(e & kVidMask);
-      a02 = (e & kA02) ? 1 : 0;
-      a12 = (e & kA12) ? 1 : 0;
-      a0 = P.rp[v2];
-      len = P.rp[v2 + 1] - a0;
-      // base counts of candidates not adjacent to v2 (rank queries)
-      const long long I_gt2 = ni - lower_bound_dev(Ibuf, ni, v2 + 1);  // |I & (v2, inf)|
-      if (a02) {
-        const int ia = lower_bound_dev(A, s, v2);  // v2 = A[ia]
-        const long long A_gt2 = s - ia - 1;        // v1 < v2, so v1 is not counted
-        add_pat<6>(c, pattern4(1, a12, 1), A_gt2 - I_gt2);        // A only, w > v2
-        add_pat<6>(c, pattern4(1, a12, 3), I_gt2);                // A & B, w > v2
-        add_pat<6>(c, pattern4(1, a12, 2), (long long)(nb - ni));  // B only, w > v0
-      } else {
-        const int ib = lower_bound_dev(B, nb, v2 + 1);
-        const long long B_gt2 = nb - ib;
-        add_pat<6>(c, pattern4(0, 1, 2), B_gt2 - I_gt2);  // B only, w > v2
-      }
-    }
-    seen += (unsigned long long)len;
-    const int incl = warp_inclusive_scan(len, lane);
-    const int total = __shfl_sync(kFull, incl, 31);
-    const int excl = incl - len;
-    for (int base = 0; base < total; base += 32) {
-      const int t = base + lane;
-      const bool active = t < total;
-      const int q = min(warp_owner(incl, t), 31);
-      const int aq = __shfl_sync(kFull, a0, q);
-      const int eq = __shfl_sync(kFull, excl, q);
-      const int32_t v2q = __shfl_sync(kFull, v2, q);
-      const int a02q = __shfl_sync(kFull, a02, q);
-      const int a12q = __shfl_sync(kFull, a12, q);
-      if (active) {
-        const int32_t w = P.col[aq + (t - eq)];
-        if (w > v0 && w != v1) {
-          const int a = (w >= amin && w <= amax && contains_dev(A, s, w)) ? 1 : 0;
-          const int b = (w >= bmin && w <= bmax && contains_dev(B, nb, w)) ? 1 : 0;
-          const int M = 4 | a | (b << 1);
-          if (!a && !b) {
-            add_pat<6>(c, pattern4(a02q, a12q, 4), 1);
-          } else if (a02q) {
-            if (!a || w > v2q) {  // adjacent to v0: needs w > v2; to v1 only: always
-              add_pat<6>(c, pattern4(1, a12q, M), 1);
-              add_pat<6>(c, pattern4(1, a12q, M & 3), -1);
-            }
-          } else if (!a && w > v2q) {  // f2 = 1, adjacent to v1 (and v2) only
-            add_pat<6>(c, pattern4(0, 1, M), 1);
-            add_pat<6>(c, pattern4(0, 1, M & 3), -1);
-          }
-        }
-      }
-    }
+  } else if (!a && w > v2) {  // f2 = 1: adjacent to v1 (and v2) only, above v2
+    add_pat<6>(c, pattern4(0, 1, M), 1);
+    add_pat<6>(c, pattern4(0, 1, M & 3), -1);
   }
 }
 
-__global__ void __launch_bounds__(512) motif_l3_warp(MotifArgs P) {
+// One level-2 edge (v0, v1) per warp at a time, taken from a device queue
+// over arcs, so heavy edges of hub vertices spread over the whole GPU.
+// A = N(v0) & (v0, inf), B = N(v1) & (v0, inf) are staged in shared memory
+// when short (else read in place, with hub bitmaps for membership);
+// I = A & B is built once per edge for the rank queries.  For each child
+// (v2, memo) the candidates adjacent to v2 are enumerated either forward
+// (scan N(v2), look up A and B) or in reverse when N(v2) is much longer
+// than A and B (scan A and B, look up N(v2)); the candidates adjacent only
+// to v2 are then its count above v0 minus the ones seen in A or B.
+__global__ void __launch_bounds__(512) motif_l3_edge(MotifArgs P) {
   extern __shared__ int32_t smem[];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  int32_t* A = smem + (int64_t)wid * 3 * P.cap;
-  int32_t* Bbuf = A + P.cap;
-  int32_t* Ibuf = Bbuf + P.cap;
+  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int32_t* Abuf = smem + (int64_t)wid * 3 * P.cap;
+  int32_t* Bbuf = Abuf + P.cap;
+  int32_t* Ismem = Bbuf + P.cap;
+  int32_t* Iglob = P.scratch + gw * P.scratch_stride;
   long long c[6] = {0, 0, 0, 0, 0, 0};
   unsigned long long seen = 0;
   int cur_g = -1;
-  const int64_t np = (int64_t)P.v_hi - P.v_lo;
+  const int64_t na = P.arc_hi - P.arc_lo;
   for (;;) {
     unsigned long long p0 = 0;
-    if (lane == 0) p0 = atomicAdd(P.queue, (unsigned long long)kMGrab);
+    if (lane == 0) p0 = atomicAdd(P.queue, (unsigned long long)kEdgeGrab);
     p0 = __shfl_sync(kFull, p0, 0);
-    if ((int64_t)p0 >= np) break;
-    const int64_t pend = min((int64_t)p0 + kMGrab, np);
-    for (int64_t pi = (int64_t)p0; pi < pend; pi++) {
-      const int32_t v0 = (int32_t)(P.v_lo + pi);
-      const int32_t u0 = P.up[v0], u1 = P.rp[v0 + 1];
-      const int s = u1 - u0;
-      if (s < 1) continue;
-      const int64_t arc0 = (int64_t)u0 - P.a_base;
-      if (P.off[arc0 + s] - P.off[arc0] == 0) continue;  // no level-3 entries below v0
-      if (s > P.cap) {
-        if (lane == 0) {
-          unsigned long long i = atomicAdd(P.queue + 2, 1ull);
-          if ((int64_t)i < P.big_cap)
-            P.big[i] = v0;
-          else
-            atomicAdd(P.err, 1ull);  // cannot happen: every vertex fits
-        }
-        continue;
-      }
-      for (int i = lane; i < s; i += 32) A[i] = P.col[u0 + i];
-      __syncwarp();
+    if ((int64_t)p0 >= na) break;
+    const int64_t pend = min((int64_t)p0 + kEdgeGrab, na);
+    for (int64_t ai = (int64_t)p0; ai < pend; ai++) {
+      const int64_t a = P.arc_lo + ai;
+      const int64_t rel = a - P.a_base;
+      const int64_t cb = P.off[rel] - P.off_shift;
+      const int64_t ce = P.off[rel + 1] - P.off_shift;
+      if (ce <= cb) continue;  // arcs to lower neighbours and childless edges
+      const int32_t v0 = P.src[a], v1 = P.col[a];
       if (P.gid) {
         const int g = P.gid[v0];
         if (g != cur_g) {
@@ -447,62 +373,137 @@ __global__ void __launch_bounds__(512) motif_l3_warp(MotifArgs P) {
           cur_g = g;
         }
       }
-      for (int j = 0; j < s; j++) l3_edge(P, A, s, j, v0, arc0, lane, Bbuf, Ibuf, c, seen);
+      const int32_t u0 = P.up[v0];
+      const int s = P.rp[v0 + 1] - u0;
+      const int hA = P.hub_idx[v0], hB = P.hub_idx[v1];
+      const int32_t* A;
+      if (s <= P.cap) {
+        for (int i = lane; i < s; i += 32) Abuf[i] = P.col[u0 + i];
+        A = Abuf;
+      } else {
+        A = P.col + u0;
+      }
+      const int32_t r0 = P.rp[v1], r1 = P.rp[v1 + 1];
+      int bstart = 0;
+      if (lane == 0) bstart = lower_bound_dev(P.col + r0, r1 - r0, v0 + 1);
+      bstart = __shfl_sync(kFull, bstart, 0);
+      const int nb = r1 - r0 - bstart;
+      const int32_t* B;
+      if (nb <= P.cap) {
+        for (int i = lane; i < nb; i += 32) Bbuf[i] = P.col[r0 + bstart + i];
+        B = Bbuf;
+      } else {
+        B = P.col + r0 + bstart;
+      }
       __syncwarp();
-    }
-  }
-  flush_patterns<6>(P, c, cur_g, lane);
-  seen = warp_sum(seen);
-  if (lane == 0 && seen) atomicAdd(P.stat, seen);
-}
-
-__global__ void __launch_bounds__(512) motif_l3_block(MotifArgs P) {
-  extern __shared__ int32_t smem[];
-  __shared__ long long sh_idx;
-  __shared__ int sh_edge;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  int32_t* stage = smem;
-  int32_t* Bbuf = smem + P.block_cap + (int64_t)wid * P.cap;
-  int32_t* Ibuf = P.scratch + ((int64_t)blockIdx.x * nw + wid) * P.scratch_stride;
-  long long c[6] = {0, 0, 0, 0, 0, 0};
-  unsigned long long seen = 0;
-  int cur_g = -1;
-  const long long nbig = min((long long)P.queue[2], (long long)P.big_cap);
-  for (;;) {
-    if (threadIdx.x == 0) {
-      sh_idx = (long long)atomicAdd(P.queue + 1, 1ull);
-      sh_edge = 0;
-    }
-    __syncthreads();
-    const long long idx = sh_idx;
-    if (idx >= nbig) break;
-    const int32_t v0 = P.big[idx];
-    const int32_t u0 = P.up[v0], u1 = P.rp[v0 + 1];
-    const int s = u1 - u0;
-    const int32_t* A;
-    if (s <= P.block_cap) {
-      for (int i = threadIdx.x; i < s; i += blockDim.x) stage[i] = P.col[u0 + i];
-      A = stage;
-    } else {
-      A = P.col + u0;
-    }
-    __syncthreads();
-    if (P.gid) {
-      const int g = P.gid[v0];
-      if (g != cur_g) {
-        flush_patterns<6>(P, c, cur_g, lane);
-        cur_g = g;
+      // I = A & B, sorted: scan the shorter list, test membership in the other
+      int32_t* I = min(s, nb) <= P.cap ? Ismem : Iglob;
+      int ni = 0;
+      {
+        const bool iterA = s <= nb;
+        const int32_t* X = iterA ? A : B;
+        const int32_t* Y = iterA ? B : A;
+        const int nx = iterA ? s : nb, ny = iterA ? nb : s;
+        const int hy = iterA ? hB : hA;
+        for (int i0 = 0; i0 < nx; i0 += 32) {
+          const int i = i0 + lane;
+          bool in = false;
+          int32_t x = 0;
+          if (i < nx) {
+            x = X[i];
+            in = member(Y, ny, hy, P, x);
+          }
+          const unsigned bal = __ballot_sync(kFull, in);
+          if (in) I[ni + __popc(bal & ((1u << lane) - 1u))] = x;
+          ni += __popc(bal);
+        }
+      }
+      __syncwarp();
+      if (lane == 0) seen += (unsigned long long)(nb + s);
+      // children, 32 at a time
+      for (int64_t c0 = cb; c0 < ce; c0 += 32) {
+        const int64_t ci = c0 + lane;
+        const bool valid = ci < ce;
+        int32_t v2 = 0, a0 = 0, d2 = 0, len = 0;
+        int a02 = 0, a12 = 0, rev = 0, hC = -1;
+        if (valid) {
+          const uint32_t e = P.l3[ci];
+          v2 = (int32_t)(e & kVidMask);
+          a02 = (e & kA02) ? 1 : 0;
+          a12 = (e & kA12) ? 1 : 0;
+          a0 = P.rp[v2];
+          d2 = P.rp[v2 + 1] - a0;
+          hC = P.hub_idx[v2];
+          // base counts of candidates not adjacent to v2 (rank queries)
+          const long long I_gt2 = ni - lower_bound_dev(I, ni, v2 + 1);  // |I & (v2, inf)|
+          if (a02) {
+            const int ia = lower_bound_dev(A, s, v2);  // v2 = A[ia]
+            const long long A_gt2 = s - ia - 1;        // v1 < v2, so v1 is not counted
+            add_pat<6>(c, pattern4(1, a12, 1), A_gt2 - I_gt2);        // A only, w > v2
+            add_pat<6>(c, pattern4(1, a12, 3), I_gt2);                // A & B, w > v2
+            add_pat<6>(c, pattern4(1, a12, 2), (long long)(nb - ni));  // B only, w > v0
+          } else {
+            const int ib = lower_bound_dev(B, nb, v2 + 1);
+            add_pat<6>(c, pattern4(0, 1, 2), (long long)(nb - ib) - I_gt2);  // B only, w > v2
+          }
+          rev = (long long)d2 > (long long)P.rev_ratio * (long long)(s + nb);
+          if (rev) {
+            // every candidate of N(v2) above v0 except v1 starts as "adjacent to v2 only";
+            // the reverse scan moves the ones also in A or B to their regions
+            const int lo = lower_bound_dev(P.col + a0, d2, v0 + 1);
+            add_pat<6>(c, pattern4(a02, a12, 4), (long long)(d2 - lo - a12));
+            len = s + nb;
+          } else {
+            len = d2;
+          }
+        }
+        seen += (unsigned long long)len;
+        const int incl = warp_inclusive_scan(len, lane);
+        const int total = __shfl_sync(kFull, incl, 31);
+        const int excl = incl - len;
+        for (int base = 0; base < total; base += 32) {
+          const int t = base + lane;
+          const bool active = t < total;
+          const int q = min(warp_owner(incl, t), 31);
+          const int aq = __shfl_sync(kFull, a0, q);
+          const int eq = __shfl_sync(kFull, excl, q);
+          const int32_t v2q = __shfl_sync(kFull, v2, q);
+          const int a02q = __shfl_sync(kFull, a02, q);
+          const int a12q = __shfl_sync(kFull, a12, q);
+          const int revq = __shfl_sync(kFull, rev, q);
+          const int d2q = __shfl_sync(kFull, d2, q);
+          const int hCq = __shfl_sync(kFull, hC, q);
+          if (!active) continue;
+          const int tq = t - eq;
+          if (!revq) {
+            const int32_t w = P.col[aq + tq];
+            if (w > v0 && w != v1) {
+              const int ia = member(A, s, hA, P, w) ? 1 : 0;
+              const int ib = member(B, nb, hB, P, w) ? 1 : 0;
+              add_c_region(c, a02q, a12q, ia, ib, w, v2q);
+            }
+          } else {
+            int32_t w;
+            int ia, ib;
+            if (tq < s) {
+              w = A[tq];
+              ia = 1;
+              if (w == v1 || w == v2q) continue;
+              ib = member(B, nb, hB, P, w) ? 1 : 0;
+            } else {
+              w = B[tq - s];
+              if (w == v2q || member(A, s, hA, P, w)) continue;  // A's copy is counted above
+              ia = 0;
+              ib = 1;
+            }
+            if (member(P.col + aq, d2q, hCq, P, w)) {
+              add_pat<6>(c, pattern4(a02q, a12q, 4), -1);  // not adjacent to v2 only
+              add_c_region(c, a02q, a12q, ia, ib, w, v2q);
+            }
+          }
+        }
       }
     }
-    const int64_t arc0 = (int64_t)u0 - P.a_base;
-    for (;;) {
-      int j = 0;
-      if (lane == 0) j = atomicAdd(&sh_edge, 1);
-      j = __shfl_sync(kFull, j, 0);
-      if (j >= s) break;
-      l3_edge(P, A, s, j, v0, arc0, lane, Bbuf, Ibuf, c, seen);
-    }
-    __syncthreads();
   }
   flush_patterns<6>(P, c, cur_g, lane);
   seen = warp_sum(seen);
@@ -573,28 +574,30 @@ struct MotifRun {
     return PGM_OK;
   }
 
-  pgm_status launch_l3(MotifArgs P, double entries) {
+  pgm_status launch_l3(MotifArgs P, int32_t pa, int32_t pb, double entries) {
     PGM_TRY_CUDA(cudaMemsetAsync(ctr() + kQ, 0, 4 * sizeof(unsigned long long), s));
     P.stat = ctr() + kStat + 3;
+    P.src = g.src;
+    P.arc_lo = g.h_rp[pa];
+    P.arc_hi = g.h_rp[pb];
+    P.hub_idx = g.hub_idx;
+    P.hub_bits = g.hub_bits;
+    P.hub_words = g.hub_words;
+    P.rev_ratio = 4;
     const int threads = o.block_threads;
     const size_t wsmem = (size_t)(threads / 32) * 3 * cap * sizeof(int32_t);
-    const size_t bsmem = ((size_t)block_cap + 16 * (size_t)cap) * sizeof(int32_t);
-    PGM_TRY(smem_attr((const void*)motif_l3_warp, 200 * 1024));
-    PGM_TRY(smem_attr((const void*)motif_l3_block, 200 * 1024));
-    const int bgrid = grid_for((const void*)motif_l3_block, 512, bsmem);
-    // per-warp scratch for I = A & B in the block kernel: |I| <= |A| <= dmax
+    PGM_TRY(smem_attr((const void*)motif_l3_edge, 200 * 1024));
+    int grid = grid_for((const void*)motif_l3_edge, threads, wsmem);
+    const int64_t na = P.arc_hi - P.arc_lo;
+    const int64_t blocks_needed = ((na + kEdgeGrab - 1) / kEdgeGrab + threads / 32 - 1) / (threads / 32);
+    grid = (int)std::max<int64_t>(1, std::min<int64_t>(grid, blocks_needed));
+    // per-warp scratch for I = A & B when both lists are long: |I| <= dmax
     P.scratch_stride = std::max<int64_t>(g.dmax, 1);
-    PGM_TRY(ws.scratch.reserve((size_t)bgrid * 16 * (size_t)P.scratch_stride));
+    PGM_TRY(ws.scratch.reserve((size_t)grid * (threads / 32) * (size_t)P.scratch_stride));
     P.scratch = ws.scratch.p;
-    const int64_t np = (int64_t)P.v_hi - P.v_lo;
-    int wgrid = grid_for((const void*)motif_l3_warp, threads, wsmem);
-    const int64_t blocks_needed = ((np + kMGrab - 1) / kMGrab + threads / 32 - 1) / (threads / 32);
-    wgrid = (int)std::max<int64_t>(1, std::min<int64_t>(wgrid, blocks_needed));
     Profiler& prof = profiler();
     int id = prof.begin("extend_sum", 3);
-    motif_l3_warp<<<wgrid, threads, wsmem, s>>>(P);
-    PGM_CHECK_LAUNCH();
-    motif_l3_block<<<bgrid, 512, bsmem, s>>>(P);
+    motif_l3_edge<<<grid, threads, wsmem, s>>>(P);
     PGM_CHECK_LAUNCH();
     prof.end(id, entries, 0.0);
     return PGM_OK;
@@ -664,7 +667,7 @@ struct MotifRun {
         W.off_shift = base;
         W.l3 = reinterpret_cast<uint32_t*>(ws.vid[3].p);
         PGM_TRY(launch_l2<mWrite>(W, "extend_write"));
-        PGM_TRY(launch_l3(W, (double)Tp));
+        PGM_TRY(launch_l3(W, pa, pb, (double)Tp));
       }
       pa = pb;
     }
