@@ -166,6 +166,9 @@ def main(argv=None):
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--scale", type=int, default=21, help="R-MAT scale (profiling runs use a smaller graph)")
+    ap.add_argument("--edges", type=int, default=28_000_000, help="R-MAT undirected edges")
     args = ap.parse_args(argv)
     if args.impl == "reference":
         return run_reference(args)
@@ -193,7 +196,10 @@ def main(argv=None):
         dist.all_reduce(t, op=op)
         return float(t.item())
 
-    g = gg.rmat21()
+    full = args.scale == 21 and args.edges == 28_000_000
+    g = gg.rmat21() if full else gg.rmat(1 << args.scale, args.edges, seed=1)
+    workload = WORKLOAD if full else WORKLOAD.replace("scale 21", f"scale {args.scale}").replace(
+        "28,000,000", f"{args.edges:,}")
     lo, hi = vertex_shares(g, world)[rank]
     stream = torch.cuda.Stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
@@ -246,7 +252,7 @@ def main(argv=None):
         return 0
 
     value = total_emb * args.steps / (total_ms * 1e-3)
-    gold = load_json(os.path.join(GOLD, "rmat21.json"))
+    gold = load_json(os.path.join(GOLD, "rmat21.json")) if full else None
     exact = None
     if gold and world == 1:
         exact = gold["clique_levels_k4"][4] == total_count
@@ -258,7 +264,7 @@ def main(argv=None):
         "metric": METRIC, "value": value, "unit": "embeddings/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "strong", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n": g.n, "m": g.m, "k": 4, "l2_flush": "256 MiB device write between steps",
+        "config": {"workload": workload, "n": g.n, "m": g.m, "k": 4, "l2_flush": "256 MiB device write between steps",
                    "embeddings_per_step": total_emb, "count": total_count, "exact_vs_oracle": exact,
                    "step_ms": [round(x, 3) for x in ms]},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
@@ -270,11 +276,12 @@ def main(argv=None):
         "clocks": clk,
     }
     # end to end through the C ABI from pinned host buffers
-    line["e2e"] = e2e(g, pgm, torch, stream, emb)
+    if not args.no_e2e:
+        line["e2e"] = e2e(g, pgm, torch, stream, emb)
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = oracle_sample(g, 4)
     G.close()
-    if not args.no_extras and world == 1:
+    if not args.no_extras and world == 1 and full:
         line["extras"] = extras(pgm, torch, stream, flush)
     print(json.dumps(line), flush=True)
     if world > 1:
