@@ -250,6 +250,32 @@ pgm_status pgm_server_poll(pgm_server *s, int64_t ticket, pgm_result *out);
 pgm_status pgm_server_drain(pgm_server *s, double timeout_s);
 void pgm_server_destroy(pgm_server *s);
 
+/* ------------------------------------------------------- no allocation */
+
+/* Triangle count of an oriented graph that the caller already holds on the
+ * device, for callers that cannot call cudaMalloc (e.g. code running under
+ * an application or framework allocator that owns all device memory, or a
+ * latency-critical caller that cannot take the device-wide synchronisation
+ * of an allocation).  No counterpart in the paper.
+ *   n, m            vertices and arcs of the DAG (m = dag_rowptr[n] < 2^31)
+ *   dag_rowptr_dev  device int32[n+1]; dag_col_dev device int32[m]: any
+ *                   acyclic orientation (each undirected edge once) with
+ *                   out-lists sorted by ascending ID, e.g. the degree
+ *                   orientation of pgm_graph_orient_by_degree
+ *   count_dev       device uint64 that receives the count
+ * Nothing is allocated: the kernels' scratch (512 B of counters and 8 MiB
+ * of hub-parent slots) is a fixed file-scope device array that every GPU
+ * loading the library holds until the process exits.  Graphs needing more
+ * hub slots than that (m / (hub_threshold + 1) + 2 > 2^20) fail with
+ * PGM_EUNSUPPORTED.  The first call on a device looks up the array's device
+ * address (make that first call before any stream capture).  All calls
+ * share the one array and clear its counters on entry: calls that overlap
+ * on the GPU race and must be serialised by the caller.  Synchronises
+ * `stream` before returning. */
+pgm_status pgm_count_triangles_noalloc(int32_t n, const int32_t *dag_rowptr_dev,
+                                       const int32_t *dag_col_dev, int64_t m,
+                                       unsigned long long *count_dev, void *stream);
+
 /* ---------------------------------------------------------------- misc */
 
 pgm_status pgm_set_options(const pgm_options *o);

@@ -116,6 +116,7 @@ _SIGS = {
     "pgm_last_error": (C.c_char_p, []),
     "pgm_version": (C.c_char_p, []),
     "pgm_kernel_launches": (C.c_uint64, []),
+    "pgm_count_triangles_noalloc": (C.c_int, [C.c_int32, P, P, C.c_int64, P, P]),
 }
 
 _lib = None
@@ -303,6 +304,15 @@ def pgm_server_drain(s: int, timeout_s: float):
 def pgm_server_destroy(s: int):
     if s:
         load().pgm_server_destroy(s)
+
+
+# ----------------------------------------------------------- no allocation
+def pgm_count_triangles_noalloc(n: int, dag_rowptr_dev_ptr: int, dag_col_dev_ptr: int, m: int,
+                                count_dev_ptr: int, stream=None):
+    """Triangle count of a caller-held device DAG, written to a caller-held
+    device uint64, without any device allocation by the library."""
+    _ok(load().pgm_count_triangles_noalloc(n, dag_rowptr_dev_ptr, dag_col_dev_ptr, m, count_dev_ptr,
+                                           _stream(stream)), "pgm_count_triangles_noalloc")
 
 
 # -------------------------------------------------------------------- misc
