@@ -367,7 +367,65 @@ def extras(pgm, torch, stream, flush):
             "exact_vs_oracle": (digest == gold["motif4_sha256"]) if gold else None}
     finally:
         pgm.pgm_batch_destroy(h)
+    out["serving_64_graphs"] = serving(pgm)
     return out
+
+
+def serving(pgm, rate=2000.0, seconds=10.0, inflight=8, budget=60 << 30):
+    """Poisson request stream against 64 resident graphs (continuous batching
+    with memory admission); latency = submission to result on the host."""
+    b = gg.serving_64()
+    gold = load_json(os.path.join(GOLD, "serving_64.json"))
+    kinds = [(pgm.PGM_Q_TRIANGLE, 3), (pgm.PGM_Q_KCLIQUE, 4), (pgm.PGM_Q_MOTIF, 3)]
+    s = pgm.pgm_server_create(budget, inflight)
+    try:
+        ids = []
+        for i in range(b.G):
+            p = b.part(i)
+            ids.append(pgm.pgm_server_add_graph(s, p.n, p.rowptr, p.col))
+        # warm-up (not timed): every query kind once on every graph
+        for gi in range(b.G):
+            for kind, k in kinds:
+                pgm.pgm_server_submit(s, kind, k, ids[gi])
+        pgm.pgm_server_drain(s, 600.0)
+        count = int(rate * seconds)
+        t_arr, qt, gs = gg.poisson_stream(count, rate, len(kinds), b.G, seed=1)
+        tickets = []
+        t0 = time.perf_counter()
+        for i in range(count):
+            while time.perf_counter() - t0 < t_arr[i]:
+                pass
+            kind, k = kinds[int(qt[i])]
+            tickets.append(pgm.pgm_server_submit(s, kind, k, ids[int(gs[i])]))
+        t_sub = time.perf_counter() - t0
+        pgm.pgm_server_drain(s, 1800.0)
+        lat, sub, fin, wrong, by_kind = [], [], [], 0, {0: [], 1: [], 2: []}
+        svc = {0: [], 1: [], 2: []}
+        for i, t in enumerate(tickets):
+            r = pgm.pgm_server_poll(s, t)
+            lat.append(r.finish_s - r.submit_s)
+            sub.append(r.submit_s)
+            fin.append(r.finish_s)
+            by_kind[int(qt[i])].append(r.finish_s - r.submit_s)
+            svc[int(qt[i])].append(r.finish_s - r.start_s)
+            if gold and r.status == pgm.PGM_OK:
+                gg_ = gold["graphs"][int(gs[i])]
+                want = [gg_["triangles"]] if qt[i] == 0 else ([gg_["k4"]] if qt[i] == 1 else gg_["motif3"])
+                wrong += [int(x) for x in r.counts[:len(want)]] != want
+            elif r.status != pgm.PGM_OK:
+                wrong += 1
+        lat = np.array(lat) * 1e3
+        span = max(fin) - min(sub)
+        names = {0: "triangle", 1: "4-clique", 2: "3-motif"}
+        return {"requests": count, "offered_rate_qps": rate, "submit_seconds": t_sub,
+                "achieved_qps": count / span, "p50_ms": float(np.percentile(lat, 50)),
+                "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()),
+                "p50_ms_by_kind": {names[k]: float(np.percentile(np.array(v) * 1e3, 50)) for k, v in by_kind.items() if v},
+                "p99_ms_by_kind": {names[k]: float(np.percentile(np.array(v) * 1e3, 99)) for k, v in by_kind.items() if v},
+                "service_ms_mean_by_kind": {names[k]: float(np.mean(v) * 1e3) for k, v in svc.items() if v},
+                "wrong_or_failed": int(wrong), "max_inflight": inflight, "budget_bytes": budget}
+    finally:
+        pgm.pgm_server_destroy(s)
 
 
 if __name__ == "__main__":

@@ -73,7 +73,9 @@ typedef struct {
   int32_t blocks_per_sm;   /* persistent-grid blocks per SM (default 0 = occupancy-derived)   */
   int64_t level_budget;    /* max entries of one materialised level chunk (edge blocking, default 1<<29) */
   int32_t profile;         /* 1 = record per-launch CUDA-event times (pgm_last_profile)       */
-  int32_t reserved[7];
+  int32_t reverse_ratio;   /* intersect in reverse (scan the shorter list, search the longer)
+                              when the longer is this many times longer (default 2)          */
+  int32_t reserved[6];
 } pgm_options;
 
 /* Per-call profile (when options.profile = 1): one record per kernel phase. */

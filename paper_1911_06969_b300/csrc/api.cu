@@ -29,7 +29,7 @@ const char* get_error() { return t_err.c_str(); }
 static std::atomic<uint64_t> g_launches{0};
 void note_launches(uint64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
-static pgm_options g_opts = {256, 512, 0, 0, (int64_t)1 << 29, 0, {0}};
+static pgm_options g_opts = {256, 512, 0, 0, (int64_t)1 << 29, 0, 2, {0}};
 
 pgm_options& options() { return g_opts; }
 
@@ -228,38 +228,51 @@ pgm_status pgm_set_options(const pgm_options* o) {
     pgm::set_error("pgm_set_options: null options");
     return PGM_EINVAL;
   }
-  pgm_options v = *o;
-  pgm_options& cur = pgm::options();
+  const pgm_options v = *o;
+  pgm_options next = pgm::options();  // validated as a whole, then applied
   if (v.block_threads) {
     if (v.block_threads < 64 || v.block_threads > 512 || v.block_threads % 32) {
       pgm::set_error("block_threads must be a multiple of 32 in [64, 512]");
       return PGM_EINVAL;
     }
-    cur.block_threads = v.block_threads;
+    next.block_threads = v.block_threads;
   }
   if (v.warp_stage_cap) {
     if (v.warp_stage_cap < 32 || v.warp_stage_cap > 4096) {
       pgm::set_error("warp_stage_cap must be in [32, 4096]");
       return PGM_EINVAL;
     }
-    cur.warp_stage_cap = v.warp_stage_cap;
+    next.warp_stage_cap = v.warp_stage_cap;
+  }
+  // shared memory of the warp kernels: (threads / 32) * cap ints per staged list
+  if ((next.block_threads / 32) * next.warp_stage_cap > 16384) {
+    pgm::set_error("block_threads / 32 * warp_stage_cap must be <= 16384 (shared memory)");
+    return PGM_EINVAL;
   }
   if (v.hub_threshold) {
     if (v.hub_threshold < 2) {
       pgm::set_error("hub_threshold must be >= 2");
       return PGM_EINVAL;
     }
-    cur.hub_threshold = v.hub_threshold;
+    next.hub_threshold = v.hub_threshold;
   }
-  if (v.blocks_per_sm) cur.blocks_per_sm = v.blocks_per_sm < 0 ? 0 : v.blocks_per_sm;
+  if (v.blocks_per_sm) next.blocks_per_sm = v.blocks_per_sm < 0 ? 0 : v.blocks_per_sm;
   if (v.level_budget) {
     if (v.level_budget < 1024) {
       pgm::set_error("level_budget must be >= 1024 entries");
       return PGM_EINVAL;
     }
-    cur.level_budget = v.level_budget;
+    next.level_budget = v.level_budget;
   }
-  cur.profile = v.profile ? 1 : 0;
+  if (v.reverse_ratio) {
+    if (v.reverse_ratio < 1) {
+      pgm::set_error("reverse_ratio must be >= 1");
+      return PGM_EINVAL;
+    }
+    next.reverse_ratio = v.reverse_ratio;
+  }
+  next.profile = v.profile ? 1 : 0;
+  pgm::options() = next;
   return PGM_OK;
 }
 

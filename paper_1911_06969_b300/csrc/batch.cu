@@ -108,6 +108,14 @@ pgm_status check_tune(const pgm_tune* t) {
     set_error("tune: warp_stage_cap must be in [32, 4096]");
     return PGM_EINVAL;
   }
+  {
+    const int th = t->block_threads ? t->block_threads : options().block_threads;
+    const int cp = t->warp_stage_cap ? t->warp_stage_cap : options().warp_stage_cap;
+    if ((th / 32) * cp > 16384) {
+      set_error("tune: block_threads / 32 * warp_stage_cap must be <= 16384 (shared memory)");
+      return PGM_EINVAL;
+    }
+  }
   if (t->hub_threshold && t->hub_threshold < 2) {
     set_error("tune: hub_threshold must be >= 2");
     return PGM_EINVAL;

@@ -123,11 +123,11 @@ struct CliqueRun {
     A.hub = hub;
     A.cap = cap;
     A.block_cap = block_cap;
-    A.rev_ratio = 4;
+    A.rev_ratio = o.reverse_ratio;
     A.gid = g.gid;
     A.per_graph = per_graph;
     const int threads = o.block_threads;
-    const size_t wsmem = (size_t)(threads / 32) * (cap + 32) * sizeof(int32_t);
+    const size_t wsmem = clique_warp_smem(threads, cap);
     const size_t bsmem = (size_t)block_cap * sizeof(int32_t) + (size_t)(512 / 32) * 32 * 4;
     const void* wfn;
     const void* bfn;

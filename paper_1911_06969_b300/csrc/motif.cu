@@ -583,7 +583,7 @@ struct MotifRun {
     P.hub_idx = g.hub_idx;
     P.hub_bits = g.hub_bits;
     P.hub_words = g.hub_words;
-    P.rev_ratio = 4;
+    P.rev_ratio = o.reverse_ratio;
     const int threads = o.block_threads;
     const size_t wsmem = (size_t)(threads / 32) * 3 * cap * sizeof(int32_t);
     PGM_TRY(smem_attr((const void*)motif_l3_edge, 200 * 1024));

@@ -107,9 +107,9 @@ extern "C" pgm_status pgm_count_triangles_noalloc(int32_t n, const int32_t* dag_
     A.hub = hub;
     A.cap = cap;
     A.block_cap = 12288;
-    A.rev_ratio = 4;
+    A.rev_ratio = o.reverse_ratio;
     const int threads = o.block_threads;
-    const size_t wsmem = (size_t)(threads / 32) * (cap + 32) * sizeof(int32_t);
+    const size_t wsmem = clique_warp_smem(threads, cap);
     const size_t bsmem = (size_t)A.block_cap * sizeof(int32_t) + (size_t)(512 / 32) * 32 * 4;
     const void* wfn = (const void*)clique_warp_kernel<kSum, int32_t>;
     const void* bfn = (const void*)clique_block_kernel<kSum, int32_t>;
