@@ -65,7 +65,9 @@ typedef struct {
   uint64_t sum_c3[2];   /* sum_v C(d_v, 3) as a 128-bit value (low, high) */
 } pgm_graph_stats;
 
-/* Tunables (pgm_set_options / pgm_get_options).  Zero keeps the current value. */
+/* Tunables (pgm_set_options / pgm_get_options).  A zero field keeps the
+ * current value, except `profile` and `clique_engine`, which every call
+ * sets (0 = off / auto). */
 typedef struct {
   int32_t block_threads;   /* threads per block of the warp-per-parent kernels, 64..512 (default 256) */
   int32_t warp_stage_cap;  /* per-warp shared-memory staging capacity, ints (default 512)     */
@@ -75,7 +77,10 @@ typedef struct {
   int32_t profile;         /* 1 = record per-launch CUDA-event times (pgm_last_profile)       */
   int32_t reverse_ratio;   /* intersect in reverse (scan the shorter list, search the longer)
                               when the longer is this many times longer (default 2)          */
-  int32_t reserved[6];
+  int32_t clique_engine;   /* 0 = auto (bitset levels for k = 4, 5; level lists otherwise),
+                              1 = level lists (vid arrays + inspection-execution),
+                              2 = bitset levels where supported                               */
+  int32_t reserved[5];
 } pgm_options;
 
 /* Per-call profile (when options.profile = 1): one record per kernel phase. */

@@ -29,7 +29,7 @@ const char* get_error() { return t_err.c_str(); }
 static std::atomic<uint64_t> g_launches{0};
 void note_launches(uint64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
-static pgm_options g_opts = {256, 512, 0, 0, (int64_t)1 << 29, 0, 2, {0}};
+static pgm_options g_opts = {256, 512, 0, 0, (int64_t)1 << 29, 0, 2, 0, {0}};
 
 pgm_options& options() { return g_opts; }
 
@@ -271,6 +271,11 @@ pgm_status pgm_set_options(const pgm_options* o) {
     }
     next.reverse_ratio = v.reverse_ratio;
   }
+  if (v.clique_engine < 0 || v.clique_engine > 2) {
+    pgm::set_error("clique_engine must be 0 (auto), 1 (level lists) or 2 (bitset levels)");
+    return PGM_EINVAL;
+  }
+  next.clique_engine = v.clique_engine;
   next.profile = v.profile ? 1 : 0;
   pgm::options() = next;
   return PGM_OK;

@@ -258,6 +258,31 @@ pgm_status count_kcliques(Graph& g, Workspace& ws, cudaStream_t s, int k, int32_
     *out = k == 1 ? (uint64_t)(v_hi - v_lo) : (uint64_t)(g.h_dag_rp[v_hi] - g.h_dag_rp[v_lo]);
     return PGM_OK;
   }
+  const int engine = options().clique_engine;
+  if ((engine == 0 && (k == 4 || k == 5)) || (engine == 2 && k >= 3 && k <= 5)) {
+    uint64_t ls[3] = {0, 0, 0};
+    const pgm_status st = count_kcliques_bitset(g, ws, s, k, v_lo, v_hi, out, per_graph_dev, ls);
+    if (st != PGM_EUNSUPPORTED) {
+      if (st != PGM_OK || current_plan()) return st;
+      Profiler& prof = profiler();
+      if (prof.on) {
+        PGM_TRY(prof.finish(&lp));
+        for (int i = 0; i < lp.nphases; i++) {
+          pgm_phase& p = lp.phase[i];
+          // out-lists of the vertex and of each out-neighbour (4 B per element) + row pointers
+          if (!strcmp(p.name, "bitset_count"))
+            p.alg_bytes = 4.0 * (double)ls[2] + 4.0 * p.entries + 8.0 * (double)(v_hi - v_lo);
+        }
+      }
+      lp.level_size[1] = (uint64_t)(v_hi - v_lo);
+      lp.level_size[2] = (uint64_t)(g.h_dag_rp[v_hi] - g.h_dag_rp[v_lo]);
+      if (k >= 4) lp.level_size[3] = ls[0];
+      if (k == 5) lp.level_size[4] = ls[1];
+      lp.level_size[k] = *out;
+      lp.chunks = 0;
+      return PGM_OK;
+    }
+  }
   PGM_TRY(ws.ctr.reserve(kSlots));
   PGM_TRY_CUDA(cudaMemsetAsync(ws.ctr.p, 0, kSlots * sizeof(unsigned long long), s));
   CliqueRun run(g, ws, s, k);

@@ -194,6 +194,9 @@ pgm_status read_counters(const unsigned long long* dev, unsigned long long* host
 // counting engines (results written on PGM_OK; per_graph_dev: batches)
 pgm_status count_kcliques(Graph& g, Workspace& ws, cudaStream_t s, int k, int32_t v_lo,
                           int32_t v_hi, uint64_t* out, unsigned long long* per_graph_dev);
+pgm_status count_kcliques_bitset(Graph& g, Workspace& ws, cudaStream_t s, int k, int32_t v_lo,
+                                 int32_t v_hi, uint64_t* out, unsigned long long* per_graph_dev,
+                                 uint64_t* level_sizes);
 pgm_status count_motifs(Graph& g, Workspace& ws, cudaStream_t s, int k, int32_t v_lo,
                         int32_t v_hi, uint64_t* out, unsigned long long* per_graph_dev);
 

@@ -81,6 +81,27 @@ def test_motifs_families(g):
         assert gpu_motifs(g, k) == oracle.formula_motifs(g, k), k
 
 
+@pytest.mark.parametrize("engine", [1, 2])
+def test_clique_engines(engine):
+    """Level lists (1) and bitset levels (2) give the same exact counts, including
+    big out-lists (block kernel) and out-lists above 512 (rows in global scratch)."""
+    import itertools
+    import math
+
+    pgm.pgm_set_options(clique_engine=engine)
+    try:
+        for g in [gg.barabasi_albert(3000, 9, seed=41), gg.rmat(1 << 12, 40000, seed=42),
+                  gg.erdos_renyi(500, 0.3, seed=43)]:
+            assert gpu_cliques(g, [3, 4, 5]) == [oracle.clique_count(g, k, "degree") for k in (3, 4, 5)], g.name
+        for n in (70, 600):
+            assert gpu_cliques(gg.complete(n), [3, 4, 5]) == [math.comb(n, k) for k in (3, 4, 5)]
+        sizes = (180, 180, 180, 180)
+        want = [sum(math.prod(c) for c in itertools.combinations(sizes, k)) for k in (3, 4, 5)]
+        assert gpu_cliques(gg.complete_multipartite(sizes), [3, 4, 5]) == want
+    finally:
+        pgm.pgm_set_options(clique_engine=0)
+
+
 def test_small_tiles_hub_paths(small_tiles):
     for g in [gg.barabasi_albert(2000, 12, seed=8), gg.complete(80), gg.rmat(1 << 12, 30000, seed=9),
               gg.complete_multipartite((30, 30, 30))]:
@@ -90,7 +111,8 @@ def test_small_tiles_hub_paths(small_tiles):
 
 
 def test_chunking_reported(small_tiles):
-    pgm.pgm_set_options(warp_stage_cap=32, hub_threshold=32, level_budget=1024, profile=1)
+    # the level-list engine materialises level 3 in budget-bounded chunks
+    pgm.pgm_set_options(warp_stage_cap=32, hub_threshold=32, level_budget=1024, profile=1, clique_engine=1)
     g = gg.barabasi_albert(3000, 10, seed=11)
     with pgm.Graph(g) as G:
         c4 = G.kcliques(4)
@@ -113,8 +135,9 @@ def test_triangle_er4096_golden():
     assert gpu_motifs(g, 4) == d["motif4"]
 
 
-def test_level_sizes_match_oracle():
-    pgm.pgm_set_options(profile=1)
+@pytest.mark.parametrize("engine", [1, 2])
+def test_level_sizes_match_oracle(engine):
+    pgm.pgm_set_options(profile=1, clique_engine=engine)
     try:
         g = gg.barabasi_albert(5000, 8, seed=12)
         lv = oracle.clique_levels(g, 5, "degree")
@@ -122,6 +145,8 @@ def test_level_sizes_match_oracle():
             assert G.kcliques(5) == lv[5]
             prof = pgm.pgm_last_profile()
             assert prof["level_size"][2:6] == lv[2:6]
+            assert G.kcliques(4) == lv[4]
+            assert pgm.pgm_last_profile()["level_size"][2:5] == lv[2:5]
             w, t = G.motifs(3)
             prof3 = pgm.pgm_last_profile()
             m4 = G.motifs(4)
@@ -130,7 +155,7 @@ def test_level_sizes_match_oracle():
         assert prof4["level_size"][3] == w + t  # |L3| = connected 3-sets
         assert prof4["level_size"][4] == sum(m4)
     finally:
-        pgm.pgm_set_options(profile=0)
+        pgm.pgm_set_options(profile=0, clique_engine=0)
 
 
 def test_range_additivity():
