@@ -80,7 +80,11 @@ typedef struct {
   int32_t clique_engine;   /* 0 = auto (bitset levels for k = 4, 5; level lists otherwise),
                               1 = level lists (vid arrays + inspection-execution),
                               2 = bitset levels where supported                               */
-  int32_t reserved[5];
+  int32_t bitset_forward_ratio;  /* bitset rows: build row i by scanning N+(P[i]) when it is at most
+                                    this many times longer than P, else by testing P in it (default 8) */
+  int32_t bitset_smem_degree;    /* bitset rows: largest out-degree whose rows live in shared memory;
+                                    64, 256, 512 or 1024 (default 1024); larger ones use global scratch */
+  int32_t reserved[3];
 } pgm_options;
 
 /* Per-call profile (when options.profile = 1): one record per kernel phase. */

@@ -29,7 +29,7 @@ const char* get_error() { return t_err.c_str(); }
 static std::atomic<uint64_t> g_launches{0};
 void note_launches(uint64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
-static pgm_options g_opts = {256, 512, 0, 0, (int64_t)1 << 29, 0, 2, 0, {0}};
+static pgm_options g_opts = {256, 512, 0, 0, (int64_t)1 << 29, 0, 2, 0, 8, 1024, {0}};
 
 pgm_options& options() { return g_opts; }
 
@@ -276,6 +276,21 @@ pgm_status pgm_set_options(const pgm_options* o) {
     return PGM_EINVAL;
   }
   next.clique_engine = v.clique_engine;
+  if (v.bitset_forward_ratio) {
+    if (v.bitset_forward_ratio < 1) {
+      pgm::set_error("bitset_forward_ratio must be >= 1");
+      return PGM_EINVAL;
+    }
+    next.bitset_forward_ratio = v.bitset_forward_ratio;
+  }
+  if (v.bitset_smem_degree) {
+    const int b = v.bitset_smem_degree;
+    if (b != 64 && b != 256 && b != 512 && b != 1024) {
+      pgm::set_error("bitset_smem_degree must be 64, 256, 512 or 1024");
+      return PGM_EINVAL;
+    }
+    next.bitset_smem_degree = b;
+  }
   next.profile = v.profile ? 1 : 0;
   pgm::options() = next;
   return PGM_OK;

@@ -55,7 +55,9 @@ class pgm_graph_stats(C.Structure):
 class pgm_options(C.Structure):
     _fields_ = [("block_threads", C.c_int32), ("warp_stage_cap", C.c_int32), ("hub_threshold", C.c_int32),
                 ("blocks_per_sm", C.c_int32), ("level_budget", C.c_int64), ("profile", C.c_int32),
-                ("reverse_ratio", C.c_int32), ("clique_engine", C.c_int32), ("reserved", C.c_int32 * 5)]
+                ("reverse_ratio", C.c_int32), ("clique_engine", C.c_int32),
+                ("bitset_forward_ratio", C.c_int32), ("bitset_smem_degree", C.c_int32),
+                ("reserved", C.c_int32 * 3)]
 
 
 class pgm_phase(C.Structure):

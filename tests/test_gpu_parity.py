@@ -102,6 +102,29 @@ def test_clique_engines(engine):
         pgm.pgm_set_options(clique_engine=0)
 
 
+@pytest.mark.parametrize("smem_degree,fwd", [(64, 1), (256, 1000), (512, 8), (1024, 1), (1024, 1000)])
+def test_bitset_buckets(smem_degree, fwd):
+    """Bitset engine: every out-degree bucket (rows in shared memory up to
+    bitset_smem_degree, global rows above it) and both row-building directions
+    give the exact counts."""
+    import itertools
+    import math
+
+    pgm.pgm_set_options(clique_engine=2, bitset_smem_degree=smem_degree, bitset_forward_ratio=fwd)
+    try:
+        for g in [gg.barabasi_albert(3000, 9, seed=41), gg.rmat(1 << 12, 40000, seed=42)]:
+            assert gpu_cliques(g, [3, 4, 5]) == [oracle.clique_count(g, k, "degree") for k in (3, 4, 5)], g.name
+        sizes = (90,) * 6  # out-degrees up to 450
+        want = [sum(math.prod(c) for c in itertools.combinations(sizes, k)) for k in (3, 4, 5)]
+        assert gpu_cliques(gg.complete_multipartite(sizes), [3, 4, 5]) == want
+        sizes = (260,) * 5  # out-degrees up to 1040: above the largest shared-memory bucket
+        want = [sum(math.prod(c) for c in itertools.combinations(sizes, k)) for k in (3, 4)]
+        assert gpu_cliques(gg.complete_multipartite(sizes), [3, 4]) == want
+        assert gpu_cliques(gg.complete(1100), [3, 4]) == [math.comb(1100, k) for k in (3, 4)]
+    finally:
+        pgm.pgm_set_options(clique_engine=0, bitset_smem_degree=1024, bitset_forward_ratio=8)
+
+
 def test_small_tiles_hub_paths(small_tiles):
     for g in [gg.barabasi_albert(2000, 12, seed=8), gg.complete(80), gg.rmat(1 << 12, 30000, seed=9),
               gg.complete_multipartite((30, 30, 30))]:
