@@ -173,9 +173,15 @@ def main(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--scale", type=int, default=21, help="R-MAT scale (profiling runs use a smaller graph)")
     ap.add_argument("--edges", type=int, default=28_000_000, help="R-MAT undirected edges")
+    ap.add_argument("--k", type=int, default=4, choices=[3, 4, 5],
+                    help="clique size of the step (profiling runs; the benchmark is k = 4)")
+    ap.add_argument("--motif-only", type=int, default=0, metavar="N",
+                    help="profiling: time only 4-motif counting on a Chung-Lu graph of N vertices")
     args = ap.parse_args(argv)
     if args.impl == "reference":
         return run_reference(args)
+    if args.motif_only:
+        return motif_only(args)
 
     import torch
     import torch.distributed as dist
@@ -204,6 +210,10 @@ def main(argv=None):
     g = gg.rmat21() if full else gg.rmat(1 << args.scale, args.edges, seed=1)
     workload = WORKLOAD if full else WORKLOAD.replace("scale 21", f"scale {args.scale}").replace(
         "28,000,000", f"{args.edges:,}")
+    k = args.k
+    if k != 4:
+        workload = workload.replace("4-clique", f"{k}-clique")
+        full = False  # the benchmark line is the 4-clique count
     lo, hi = vertex_shares(g, world)[rank]
     stream = torch.cuda.Stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
@@ -212,12 +222,12 @@ def main(argv=None):
     pgm.pgm_set_options(profile=1)
 
     def step():
-        return pgm.pgm_count_kcliques_range(G.h, 4, lo, hi)
+        return pgm.pgm_count_kcliques_range(G.h, k, lo, hi)
 
     for _ in range(args.warmup):
         count = step()
     prof = pgm.pgm_last_profile()
-    emb = sum(prof["level_size"][2:5])  # |L2| + |L3| + |L4| of this rank's share
+    emb = sum(prof["level_size"][2:k + 1])  # |L2| + ... + |Lk| of this rank's share
 
     clocks = ClockSampler(local)
     barrier()
@@ -271,7 +281,7 @@ def main(argv=None):
         "metric": METRIC, "value": value, "unit": "embeddings/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "strong", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-        "config": {"workload": workload, "n": g.n, "m": g.m, "k": 4, "l2_flush": "256 MiB device write between steps",
+        "config": {"workload": workload, "n": g.n, "m": g.m, "k": k, "l2_flush": "256 MiB device write between steps",
                    "embeddings_per_step": total_emb, "count": total_count, "exact_vs_oracle": exact,
                    "step_ms": [round(x, 3) for x in ms]},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
@@ -293,6 +303,34 @@ def main(argv=None):
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+    return 0
+
+
+def motif_only(args):
+    """4-motif counting alone on a Chung-Lu graph (exponent 2.1, mean weight
+    10, weights capped at 20,000) of --motif-only vertices: a small case of
+    the motif kernels for profiling."""
+    import torch
+
+    from paper_1911_06969_b300 import pgm
+
+    n = args.motif_only
+    g = gg.chung_lu_1m() if n == 1 << 20 else gg.chung_lu(n, 2.1, 10.0, 20000.0, 1)
+    stream = torch.cuda.Stream()
+    with pgm.Graph(g, stream=stream) as G:
+        for _ in range(args.warmup):
+            m4 = G.motifs(4)
+        ms = []
+        for _ in range(args.steps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            m4 = G.motifs(4)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+    print(json.dumps({"workload": f"4-motif count, Chung-Lu n={n}", "n": g.n, "m": g.m, "counts": m4,
+                      "ms": [round(x, 3) for x in ms]}), flush=True)
     return 0
 
 

@@ -75,48 +75,105 @@ __device__ __forceinline__ void bm_flush(const BmArgs& B, unsigned long long (&c
   }
 }
 
-// position of x in the sorted list P (length d), or -1
-__device__ __forceinline__ int find_pos(const int32_t* P, int d, int32_t x) {
-  if (d == 0 || x < P[0] || x > P[d - 1]) return -1;
-  const int i = lower_bound_dev(P, d, x);
-  return (i < d && P[i] == x) ? i : -1;
+// Lower bound of x in the sorted list P[0, d), d >= 1, with a trip count
+// that depends on d only (the lanes of a warp never diverge in the loop).
+__device__ __forceinline__ int bm_lower_bound(const int32_t* P, int d, int32_t x) {
+  int base = 0, n = d;
+  while (n > 1) {
+    const int half = n >> 1;
+    base = P[base + half] < x ? base + half : base;
+    n -= half;
+  }
+  return base + (P[base] < x ? 1 : 0);
 }
 
-// Build rows R_i (i in [i0, i1), step `step`) of vertex set P (length d) into
-// rows[i * stride + w]; one warp per row, lanes scan the shorter side.
-// Rows must be zeroed beforehand (forward sets bits with atomicOr).
-__device__ __forceinline__ void build_rows(const BmArgs& B, const int32_t* P, int d, uint32_t* rows,
-                                           int stride, int i0, int i1, int step, int lane,
-                                           unsigned long long& seen) {
-  for (int i = i0; i < i1; i += step) {
-    const int32_t v = P[i];
-    const int32_t a0 = B.rp[v], dv = B.rp[v + 1] - a0;
-    uint32_t* row = rows + (int64_t)i * stride;
-    if (lane == 0) seen += (unsigned long long)dv;
-    if (dv <= 2 * d) {
-      // forward: each out-neighbour of v found in P sets its bit
-      for (int t = lane; t < dv; t += 32) {
-        const int j = find_pos(P, d, B.col[a0 + t]);
-        if (j >= 0) atomicOr(row + (j >> 5), 1u << (j & 31));
-      }
-    } else {
-      // reverse: one ballot word per 32 positions of P
-      for (int j0 = 0; j0 < d; j0 += 32) {
-        const int j = j0 + lane;
-        const bool in = j < d && contains_dev(B.col + a0, dv, P[j]);
-        const unsigned b = __ballot_sync(kFull, in);
-        if (lane == 0 && b) row[j0 >> 5] |= b;
+// One-hash bitmap filter over the vertices of P: bit h(x) is set for every
+// x in P, so a clear bit proves that x is not in P (a set bit may be a
+// collision).  The filter has 32 * FW bits, FW = 2^fb >= d words.
+__device__ __forceinline__ uint32_t bm_fhash(int32_t x, int fshift) {
+  return ((uint32_t)x * 0x9E3779B1u) >> fshift;
+}
+
+__device__ __forceinline__ bool bm_fhit(const uint32_t* F, int fshift, int32_t x) {
+  const uint32_t h = bm_fhash(x, fshift);
+  return (F[h >> 5] >> (h & 31)) & 1u;
+}
+
+// Filter words and shift for a list of d entries (at most `cap` words).
+__device__ __forceinline__ void bm_filter_size(int d, int cap, int& fw, int& fshift) {
+  fw = 32;
+  while (fw < d && fw < cap) fw <<= 1;
+  fshift = 32 - (__ffs(fw) - 1) - 5;  // 32 * fw bits
+}
+
+// Sets bit j of `row` when P[j] == x.
+__device__ __forceinline__ void bm_locate(const int32_t* P, int d, int32_t x, uint32_t* row) {
+  const int j = bm_lower_bound(P, d, x);
+  if (j < d && P[j] == x) atomicOr(row + (j >> 5), 1u << (j & 31));
+}
+
+// Forward build of one row by one warp: scan N+(v) (col[b0, b0 + dv)),
+// reject elements with the filter, queue the survivors in q (64 entries)
+// and locate them 32 at a time, so that the binary searches run on full
+// warps.  The row must be zero beforehand.
+__device__ __forceinline__ void bm_row_forward(const int32_t* __restrict__ col, int32_t b0, int32_t dv,
+                                               const int32_t* P, int d, const uint32_t* F, int fshift,
+                                               int32_t* q, uint32_t* row, int lane) {
+  constexpr int U = 4;  // loads in flight per lane
+  const unsigned lt = (1u << lane) - 1u;
+  int cnt = 0;
+  for (int t0 = 0; t0 < dv; t0 += 32 * U) {
+    int32_t x[U];
+#pragma unroll
+    for (int r = 0; r < U; r++) {
+      const int t = t0 + r * 32 + lane;
+      x[r] = t < dv ? col[b0 + t] : -1;
+    }
+#pragma unroll
+    for (int r = 0; r < U; r++) {
+      const bool cand = x[r] >= 0 && bm_fhit(F, fshift, x[r]);
+      const unsigned bal = __ballot_sync(kFull, cand);
+      if (cand) q[cnt + __popc(bal & lt)] = x[r];
+      cnt += __popc(bal);
+      if (cnt >= 32) {
+        __syncwarp();
+        bm_locate(P, d, q[lane], row);
+        __syncwarp();
+        if (lane < cnt - 32) q[lane] = q[lane + 32];
+        cnt -= 32;
+        __syncwarp();
       }
     }
+  }
+  __syncwarp();
+  if (lane < cnt) bm_locate(P, d, q[lane], row);
+  __syncwarp();
+}
+
+// Reverse build of one row by one warp: test each P[j] against N+(v) by
+// binary search in global memory; one ballot word per 32 positions.
+__device__ __forceinline__ void bm_row_reverse(const int32_t* __restrict__ col, int32_t b0, int32_t dv,
+                                               const int32_t* P, int d, uint32_t* row, int lane) {
+  for (int j0 = 0; j0 < d; j0 += 32) {
+    const int j = j0 + lane;
+    const bool in = j < d && contains_dev(col + b0, dv, P[j]);
+    const unsigned bal = __ballot_sync(kFull, in);
+    if (lane == 0 && bal) row[j0 >> 5] |= bal;
   }
 }
 
 // ----------------------------------------------------------- warp kernel
 // One vertex per warp, d <= 64: P and the rows (2 words, stride 2) in shared memory.
-__global__ void __launch_bounds__(256) bm_warp_kernel(BmArgs B) {
+__global__ void __launch_bounds__(256, 6) bm_warp_kernel(BmArgs B) {
   __shared__ int32_t sP[8][kBmWarpD];
+  __shared__ int32_t sB0[8][kBmWarpD];
+  __shared__ int32_t sDv[8][kBmWarpD];
   __shared__ uint32_t sR[8][kBmWarpD * 2];
+  __shared__ uint32_t sF[8][kBmWarpD];  // filter: 64 words = 2048 bits
+  __shared__ int32_t sQ[8][64];         // forward-build queue
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  uint32_t* F = sF[wid];
+  constexpr int kWarpFShift = 32 - 11;
   int32_t* P = sP[wid];
   uint32_t* R = sR[wid];
   unsigned long long c[3] = {0, 0, 0};
@@ -152,10 +209,29 @@ __global__ void __launch_bounds__(256) bm_warp_kernel(BmArgs B) {
           cur_g = g;
         }
       }
-      for (int i = lane; i < d; i += 32) P[i] = B.col[a0 + i];
+      for (int i = lane; i < d; i += 32) {
+        const int32_t x = B.col[a0 + i];
+        const int32_t b = B.rp[x];
+        P[i] = x;
+        sB0[wid][i] = b;
+        sDv[wid][i] = B.rp[x + 1] - b;
+      }
       for (int i = lane; i < 2 * kBmWarpD; i += 32) R[i] = 0;
+      for (int i = lane; i < kBmWarpD; i += 32) F[i] = 0;
       __syncwarp();
-      build_rows(B, P, d, R, 2, 0, d, 1, lane, seen);
+      for (int i = lane; i < d; i += 32) {
+        const uint32_t h = bm_fhash(P[i], kWarpFShift);
+        atomicOr(F + (h >> 5), 1u << (h & 31));
+      }
+      __syncwarp();
+      for (int i = 0; i < d; i++) {
+        const int32_t b0 = sB0[wid][i], dv = sDv[wid][i];
+        if (lane == 0) seen += (unsigned long long)dv;
+        if ((int64_t)dv <= (int64_t)B.fwd_ratio * d)
+          bm_row_forward(B.col, b0, dv, P, d, F, kWarpFShift, sQ[wid], R + 2 * i, lane);
+        else
+          bm_row_reverse(B.col, b0, dv, P, d, R + 2 * i, lane);
+      }
       __syncwarp();
       // lanes own rows i = lane, lane + 32
       for (int i = lane; i < d; i += 32) {
@@ -203,29 +279,12 @@ __global__ void __launch_bounds__(256) bm_warp_kernel(BmArgs B) {
 
 // ---------------------------------------------------------- block kernels
 // One big vertex (d > 64) per block, in buckets by out-degree so that the
-// block size and shared memory fit the rows: DMAX > 0 keeps P, a hash map
-// from vertex to position in P, and the rows (W words at stride W + 1, odd
-// so that rows spread over the banks) in shared memory; DMAX = 0 keeps P
-// and the rows in global memory (the per-block scratch) and finds
-// positions by binary search.
-
-// Open-addressing hash map from vertex to its position in P (linear
-// probing, at most a quarter full, so the table always has empty slots).
-__device__ __forceinline__ uint32_t bm_hash(int32_t x, int shift) {
-  return ((uint32_t)x * 0x9E3779B1u) >> shift;
-}
-
-__device__ __forceinline__ int bm_hfind(const int32_t* key, const uint16_t* pos, uint32_t mask, int shift,
-                                        int32_t x) {
-  uint32_t h = bm_hash(x, shift);
-  for (uint32_t probe = 0; probe <= mask; probe++) {
-    const int32_t k = key[h];
-    if (k == x) return pos[h];
-    if (k < 0) return -1;
-    h = (h + 1) & mask;
-  }
-  return -1;
-}
+// block size and shared memory fit the rows: DMAX > 0 keeps P, the start
+// and length of each out-list, the filter and the rows (W words at stride
+// W + 1, odd so that rows spread over the banks) in shared memory; DMAX = 0
+// keeps P and the rows in global memory (the per-block scratch) and the
+// filter (at most kBmGlobalFW words) in shared memory.
+constexpr int kBmGlobalFW = 8192;
 
 // Set bits of a row, 32 at a time: appends the set bits of the 32 words
 // held one per lane (`mine`, words w0 .. w0 + 31) to the warp's buffer
@@ -261,14 +320,33 @@ __device__ __forceinline__ void bm_bits_tail(const int* buf, int cnt, int lane, 
   __syncwarp();
 }
 
+// Row layout of the block kernels: a row of W words occupies S4 16-byte
+// chunks, S4 = ceil(W / 4) rounded up to an odd number, so that rows can be
+// read with 128-bit loads and the rows taken by the 8 lanes of a
+// quarter-warp (one j each) fall on different bank groups unless their
+// indices agree modulo 8.
+__host__ __device__ constexpr int bm_s4(int W) { return ((W + 3) >> 2) | 1; }
+
+// |X & Y| over n4 16-byte chunks.
+__device__ __forceinline__ unsigned bm_and_popc4(const uint4* X, const uint4* Y, int n4) {
+  unsigned s = 0;
+#pragma unroll 2
+  for (int q = 0; q < n4; q++) {
+    const uint4 x = X[q], y = Y[q];
+    s += __popc(x.x & y.x) + __popc(x.y & y.y) + __popc(x.z & y.z) + __popc(x.w & y.w);
+  }
+  return s;
+}
+
 // Shared-memory bytes of bm_block_kernel<DMAX, THREADS>.
 __host__ __device__ constexpr size_t bm_block_smem(int dmax, int threads) {
   return dmax > 0 ? (size_t)4 * dmax                       // P
-                        + (size_t)(4 + 2) * 4 * dmax        // hash keys + positions (4 dmax slots)
-                        + (size_t)4 * (threads / 32) * 128  // two 64-entry bit buffers per warp
-                        + (size_t)4 * (threads / 32) * (dmax / 32 + 1)  // C = R_i & R_j per warp
-                        + (size_t)4 * dmax * (dmax / 32 + 1)            // rows
-                  : (size_t)4 * (threads / 32) * 128;
+                        + (size_t)8 * dmax                  // start and length of each out-list
+                        + (size_t)4 * dmax                  // filter (up to dmax words)
+                        + (size_t)4 * (threads / 32) * 128  // two 64-entry buffers per warp
+                        + (size_t)16 * (threads / 32) * bm_s4(dmax / 32)  // C = R_i & R_j per warp
+                        + (size_t)16 * dmax * bm_s4(dmax / 32)            // rows
+                  : (size_t)4 * (threads / 32) * 128 + (size_t)4 * kBmGlobalFW;
 }
 
 // resident blocks per SM that the register budget is sized for
@@ -276,21 +354,25 @@ __host__ __device__ constexpr int bm_min_blocks(int dmax, int threads) {
   return dmax == 0 ? 2 : (threads <= 256 ? 6 : (threads <= 512 ? 3 : 1));
 }
 
-template <int DMAX, int THREADS>
+// FIVE selects the 5-clique variant (k = 5); the other handles k = 3 and 4.
+template <int DMAX, int THREADS, bool FIVE>
 __global__ void __launch_bounds__(THREADS, bm_min_blocks(DMAX, THREADS)) bm_block_kernel(BmArgs B, int bucket) {
   constexpr int NW = THREADS / 32;
-  constexpr int HT = 4 * DMAX;
-  extern __shared__ uint32_t smem_u[];
+  constexpr int S4MAX = DMAX > 0 ? bm_s4(DMAX / 32) : 0;
+  extern __shared__ __align__(16) uint32_t smem_u[];
   __shared__ long long sh_idx;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  // layout (DMAX > 0): P | B0 | Dv | filter | buffers | C | rows;
+  // (DMAX = 0): filter | buffers
+  constexpr int kHead = DMAX > 0 ? 4 * DMAX : kBmGlobalFW;
   int32_t* sP = reinterpret_cast<int32_t*>(smem_u);
-  int32_t* sKey = sP + DMAX;
-  uint16_t* sPos = reinterpret_cast<uint16_t*>(sKey + HT);
-  int* buf = reinterpret_cast<int*>(smem_u) + (DMAX > 0 ? DMAX + HT + HT / 2 : 0) + wid * 128;
+  int32_t* sB0 = sP + DMAX;
+  int32_t* sDv = sB0 + DMAX;
+  uint32_t* sF = smem_u + (DMAX > 0 ? 3 * DMAX : 0);
+  int* buf = reinterpret_cast<int*>(smem_u) + kHead + wid * 128;
   int* buf2 = buf + 64;
-  uint32_t* sC = reinterpret_cast<uint32_t*>(smem_u) + (DMAX > 0 ? DMAX + HT + HT / 2 : 0) + NW * 128 +
-                 wid * (DMAX / 32 + 1);
-  uint32_t* sRows = reinterpret_cast<uint32_t*>(smem_u) + DMAX + HT + HT / 2 + NW * 128 + NW * (DMAX / 32 + 1);
+  uint32_t* sC = smem_u + kHead + NW * 128 + wid * 4 * S4MAX;
+  uint32_t* sRows = smem_u + kHead + NW * 128 + NW * 4 * S4MAX;
   uint32_t* gRows = B.scratch ? B.scratch + (int64_t)blockIdx.x * B.scratch_words : nullptr;
   unsigned long long c[3] = {0, 0, 0};
   unsigned long long seen = 0;
@@ -306,7 +388,7 @@ __global__ void __launch_bounds__(THREADS, bm_min_blocks(DMAX, THREADS)) bm_bloc
     const int32_t u = big[idx];
     const int32_t a0 = B.rp[u];
     const int d = B.rp[u + 1] - a0;
-    const int W = (d + 31) >> 5, stride = W + 1;
+    const int W = (d + 31) >> 5, n4 = (W + 3) >> 2, S = 4 * bm_s4(W);
     if (B.gid) {
       const int g = B.gid[u];
       if (g != cur_g) {
@@ -316,200 +398,110 @@ __global__ void __launch_bounds__(THREADS, bm_min_blocks(DMAX, THREADS)) bm_bloc
     }
     const int32_t* P;
     uint32_t* R;
-    uint32_t hmask = 0;
-    int hshift = 0;
+    int fw, fshift;
+    bm_filter_size(d, DMAX > 0 ? DMAX : kBmGlobalFW, fw, fshift);
     if constexpr (DMAX > 0) {
-      int T = 32;
-      while (T < 4 * d) T <<= 1;
-      hmask = (uint32_t)T - 1u;
-      hshift = 32 - __ffs(T) + 1;
-      for (int i = threadIdx.x; i < d; i += THREADS) sP[i] = B.col[a0 + i];
-      for (int i = threadIdx.x; i < T; i += THREADS) sKey[i] = -1;
-      for (int i = threadIdx.x; i < d * stride; i += THREADS) sRows[i] = 0;
-      __syncthreads();
       for (int i = threadIdx.x; i < d; i += THREADS) {
-        const int32_t x = sP[i];
-        uint32_t h = bm_hash(x, hshift);
-        for (int probe = 0; probe < T; probe++) {
-          if (atomicCAS(sKey + h, -1, x) == -1) {
-            sPos[h] = (uint16_t)i;
-            break;
-          }
-          h = (h + 1) & hmask;
-        }
+        const int32_t x = B.col[a0 + i];
+        const int32_t b = B.rp[x];
+        sP[i] = x;
+        sB0[i] = b;
+        sDv[i] = B.rp[x + 1] - b;
       }
+      for (int i = threadIdx.x; i < d * S; i += THREADS) sRows[i] = 0;
       P = sP;
       R = sRows;
     } else {
-      for (int64_t i = threadIdx.x; i < (int64_t)d * stride; i += THREADS) gRows[i] = 0;
+      for (int64_t i = threadIdx.x; i < (int64_t)d * S; i += THREADS) gRows[i] = 0;
       P = B.col + a0;
       R = gRows;
     }
+    for (int i = threadIdx.x; i < fw; i += THREADS) sF[i] = 0;
+    __syncthreads();
+    for (int i = threadIdx.x; i < d; i += THREADS) {
+      const uint32_t h = bm_fhash(P[i], fshift);
+      atomicOr(sF + (h >> 5), 1u << (h & 31));
+    }
     __syncthreads();
     // rows R_i = N+(P[i]) & P, one warp per row
-    const int32_t plo = P[0], phi = P[d - 1];
     for (int i = wid; i < d; i += NW) {
-      const int32_t v = P[i];
-      const int32_t b0 = B.rp[v], dv = B.rp[v + 1] - b0;
-      uint32_t* row = R + (int64_t)i * stride;
-      if (lane == 0) seen += (unsigned long long)dv;
-      if (dv <= B.fwd_ratio * d) {
-        // forward: each out-neighbour of v found in P sets its bit
-        for (int t0 = 0; t0 < dv; t0 += 128) {
-          int32_t x[4];
-#pragma unroll
-          for (int r = 0; r < 4; r++) {
-            const int t = t0 + r * 32 + lane;
-            x[r] = t < dv ? B.col[b0 + t] : -1;
-          }
-#pragma unroll
-          for (int r = 0; r < 4; r++) {
-            if (x[r] < plo || x[r] > phi) continue;
-            int j;
-            if constexpr (DMAX > 0) {
-              j = bm_hfind(sKey, sPos, hmask, hshift, x[r]);
-            } else {
-              j = find_pos(P, d, x[r]);
-            }
-            if (j >= 0) atomicOr(row + (j >> 5), 1u << (j & 31));
-          }
-        }
+      int32_t b0, dv;
+      if constexpr (DMAX > 0) {
+        b0 = sB0[i];
+        dv = sDv[i];
       } else {
-        // reverse: one ballot word per 32 positions of P
-        for (int j0 = 0; j0 < d; j0 += 32) {
-          const int j = j0 + lane;
-          const bool in = j < d && contains_dev(B.col + b0, dv, P[j]);
-          const unsigned bal = __ballot_sync(kFull, in);
-          if (lane == 0 && bal) row[j0 >> 5] |= bal;
-        }
+        const int32_t v = P[i];
+        b0 = B.rp[v];
+        dv = B.rp[v + 1] - b0;
       }
+      uint32_t* row = R + (int64_t)i * S;
+      if (lane == 0) seen += (unsigned long long)dv;
+      if ((int64_t)dv <= (int64_t)B.fwd_ratio * d)
+        bm_row_forward(B.col, b0, dv, P, d, sF, fshift, buf, row, lane);
+      else
+        bm_row_reverse(B.col, b0, dv, P, d, row, lane);
     }
     __syncthreads();
     // level 3 and beyond: one warp per row i
+    uint32_t* C = DMAX > 0 ? sC : gRows + (int64_t)d * S + (int64_t)wid * S;  // R_i & R_j (5-cliques)
+    // row j (32-bit offsets when the rows are in shared memory)
+    auto row4 = [&](int j) {
+      return reinterpret_cast<const uint4*>(DMAX > 0 ? R + j * S : R + (int64_t)j * S);
+    };
     for (int i = wid; i < d; i += NW) {
-      const uint32_t* Ri = R + (int64_t)i * stride;
-      if constexpr (DMAX > 0) {
-        // W <= 32: word w of R_i is held by lane w
-        const uint32_t ri = lane < W ? Ri[lane] : 0u;
-        if (B.k == 3) {
-          c[0] += (unsigned long long)__popc(ri);
-          continue;
+      const uint32_t* Ri = reinterpret_cast<const uint32_t*>(row4(i));
+      const uint4* Ri4 = row4(i);
+      unsigned tri = 0;
+      for (int w = lane; w < W; w += 32) tri += __popc(Ri[w]);
+      if (B.k == 3) {
+        c[0] += tri;
+        continue;
+      }
+      c[1] += tri;
+      int cnt = 0;
+      if constexpr (!FIVE) {
+        // 4-cliques: |R_i & R_j| for every j in R_i, one j per lane
+        auto f4 = [&](int j, bool valid) {
+          if (valid) c[0] += bm_and_popc4(Ri4, row4(j), n4);
+        };
+        for (int w0 = 0; w0 < W; w0 += 32) {
+          const uint32_t mine = w0 + lane < W ? Ri[w0 + lane] : 0u;
+          bm_bits(mine, w0, buf, cnt, lane, f4);
         }
-        c[1] += (unsigned long long)__popc(ri);
-        const uint32_t nzi = __ballot_sync(kFull, ri != 0u);
-        if (!nzi) continue;
-        int cnt = 0;
-        if (B.k == 4) {
-          // 4-cliques: |R_i & R_j| for every j in R_i, one j per lane
-          auto f4 = [&](int j, bool valid) {
-            if (!valid) return;
-            const uint32_t* Rj = R + (int64_t)j * stride;
-            unsigned s = 0;
-            for (uint32_t m = nzi; m; m &= m - 1) {
-              const int w = __ffs(m) - 1;
-              s += __popc(Ri[w] & Rj[w]);
-            }
-            c[0] += s;
-          };
-          bm_bits(ri, 0, buf, cnt, lane, f4);
-          bm_bits_tail(buf, cnt, lane, f4);
-        } else {
-          // 5-cliques: for each j in R_i (one at a time), C = R_i & R_j held
-          // one word per lane; then |C & R_l| for every l in C, one l per lane
-          auto f5 = [&](int j, bool valid) {
-            for (unsigned mq = __ballot_sync(kFull, valid); mq; mq &= mq - 1) {
-              const int q = __ffs(mq) - 1;
-              const int jq = __shfl_sync(kFull, j, q);
-              const uint32_t* Rj = R + (int64_t)jq * stride;
-              const uint32_t cw = lane < W ? (ri & Rj[lane]) : 0u;
-              c[2] += (unsigned long long)__popc(cw);
-              const uint32_t nzc = __ballot_sync(kFull, cw != 0u);
-              if (!nzc) continue;
-              if (lane < W) sC[lane] = cw;
-              __syncwarp();
-              int cnt2 = 0;
-              auto f5l = [&](int l, bool v2) {
-                if (!v2) return;
-                const uint32_t* Rl = R + (int64_t)l * stride;
-                unsigned s = 0;
-                for (uint32_t m = nzc; m; m &= m - 1) {
-                  const int w = __ffs(m) - 1;
-                  s += __popc(sC[w] & Rl[w]);
-                }
-                c[0] += s;
-              };
-              bm_bits(cw, 0, buf2, cnt2, lane, f5l);
-              bm_bits_tail(buf2, cnt2, lane, f5l);
-            }
-          };
-          bm_bits(ri, 0, buf, cnt, lane, f5);
-          bm_bits_tail(buf, cnt, lane, f5);
-        }
+        bm_bits_tail(buf, cnt, lane, f4);
       } else {
-        // rows in global memory, W > 32 words
-        unsigned long long tri = 0;
-        for (int w = lane; w < W; w += 32) tri += (unsigned long long)__popc(Ri[w]);
-        if (B.k == 3) {
-          c[0] += tri;
-          continue;
-        }
-        c[1] += tri;
-        int cnt = 0;
-        if (B.k == 4) {
-          auto f4 = [&](int j, bool valid) {
-            if (!valid) return;
-            const uint32_t* Rj = R + (int64_t)j * stride;
-            unsigned long long s = 0;
-            for (int w = 0; w < W; w++) {
-              const uint32_t x = Ri[w];
-              if (x) s += (unsigned long long)__popc(x & Rj[w]);
+        // 5-cliques: for each j in R_i (one at a time), C = R_i & R_j; then
+        // |C & R_l| for every l in C, one l per lane
+        auto f5 = [&](int j, bool valid) {
+          for (unsigned mq = __ballot_sync(kFull, valid); mq; mq &= mq - 1) {
+            const int q = __ffs(mq) - 1;
+            const int jq = __shfl_sync(kFull, j, q);
+            const uint32_t* Rj = reinterpret_cast<const uint32_t*>(row4(jq));
+            unsigned cnt4 = 0;
+            for (int w = lane; w < 4 * n4; w += 32) {
+              const uint32_t x = Ri[w] & Rj[w];  // padding words are zero
+              C[w] = x;
+              cnt4 += __popc(x);
             }
-            c[0] += s;
-          };
-          for (int w0 = 0; w0 < W; w0 += 32) {
-            const uint32_t mine = w0 + lane < W ? Ri[w0 + lane] : 0u;
-            bm_bits(mine, w0, buf, cnt, lane, f4);
-          }
-          bm_bits_tail(buf, cnt, lane, f4);
-        } else {
-          uint32_t* C = gRows + (int64_t)d * stride + (int64_t)wid * stride;
-          auto f5 = [&](int j, bool valid) {
-            for (unsigned mq = __ballot_sync(kFull, valid); mq; mq &= mq - 1) {
-              const int q = __ffs(mq) - 1;
-              const int jq = __shfl_sync(kFull, j, q);
-              const uint32_t* Rj = R + (int64_t)jq * stride;
-              unsigned long long cnt4 = 0;
-              for (int w = lane; w < W; w += 32) {
-                const uint32_t x = Ri[w] & Rj[w];
-                C[w] = x;
-                cnt4 += (unsigned long long)__popc(x);
-              }
-              c[2] += cnt4;
-              __syncwarp();
-              int cnt2 = 0;
-              auto f5l = [&](int l, bool v2) {
-                if (!v2) return;
-                const uint32_t* Rl = R + (int64_t)l * stride;
-                unsigned long long s = 0;
-                for (int w = 0; w < W; w++) {
-                  const uint32_t x = C[w];
-                  if (x) s += (unsigned long long)__popc(x & Rl[w]);
-                }
-                c[0] += s;
-              };
-              for (int w0 = 0; w0 < W; w0 += 32) {
-                const uint32_t mine = w0 + lane < W ? C[w0 + lane] : 0u;
-                bm_bits(mine, w0, buf2, cnt2, lane, f5l);
-              }
-              bm_bits_tail(buf2, cnt2, lane, f5l);
+            c[2] += cnt4;
+            __syncwarp();
+            int cnt2 = 0;
+            auto f5l = [&](int l, bool v2) {
+              if (v2)
+                c[0] += bm_and_popc4(reinterpret_cast<const uint4*>(C), row4(l), n4);
+            };
+            for (int w0 = 0; w0 < W; w0 += 32) {
+              const uint32_t mine = w0 + lane < W ? C[w0 + lane] : 0u;
+              bm_bits(mine, w0, buf2, cnt2, lane, f5l);
             }
-          };
-          for (int w0 = 0; w0 < W; w0 += 32) {
-            const uint32_t mine = w0 + lane < W ? Ri[w0 + lane] : 0u;
-            bm_bits(mine, w0, buf, cnt, lane, f5);
+            bm_bits_tail(buf2, cnt2, lane, f5l);
           }
-          bm_bits_tail(buf, cnt, lane, f5);
+        };
+        for (int w0 = 0; w0 < W; w0 += 32) {
+          const uint32_t mine = w0 + lane < W ? Ri[w0 + lane] : 0u;
+          bm_bits(mine, w0, buf, cnt, lane, f5);
         }
+        bm_bits_tail(buf, cnt, lane, f5);
       }
     }
     __syncthreads();
@@ -541,18 +533,24 @@ pgm_status count_kcliques_bitset(Graph& g, Workspace& ws, cudaStream_t s, int k,
     size_t smem;
     int grid;
   };
+  const bool five = k == 5;
   Kern kern[kBmBuckets] = {
-      {(const void*)bm_block_kernel<256, 256>, 256, bm_block_smem(256, 256), 0},
-      {(const void*)bm_block_kernel<512, 512>, 512, bm_block_smem(512, 512), 0},
-      {(const void*)bm_block_kernel<1024, 1024>, 1024, bm_block_smem(1024, 1024), 0},
-      {(const void*)bm_block_kernel<0, 512>, 512, bm_block_smem(0, 512), 0},
+      {five ? (const void*)bm_block_kernel<256, 256, true> : (const void*)bm_block_kernel<256, 256, false>, 256,
+       bm_block_smem(256, 256), 0},
+      {five ? (const void*)bm_block_kernel<512, 512, true> : (const void*)bm_block_kernel<512, 512, false>, 512,
+       bm_block_smem(512, 512), 0},
+      {five ? (const void*)bm_block_kernel<1024, 1024, true> : (const void*)bm_block_kernel<1024, 1024, false>,
+       1024, bm_block_smem(1024, 1024), 0},
+      {five ? (const void*)bm_block_kernel<0, 512, true> : (const void*)bm_block_kernel<0, 512, false>, 512,
+       bm_block_smem(0, 512), 0},
   };
+
   for (int b = 0; b < kBmBuckets; b++) {
     PGM_TRY(smem_attr(kern[b].fn, (int)kern[b].smem));
     kern[b].grid = grid_for(kern[b].fn, kern[b].threads, kern[b].smem);
   }
-  // global-row bucket: d * (W + 1) row words plus 16 warps' C buffers per block
-  const int64_t words = dmax > smem_d ? (dmax + 16) * (Wmax + 1) : 0;
+  // global-row bucket: d rows plus 16 warps' C buffers per block, 4 * S4 words each
+  const int64_t words = dmax > smem_d ? (dmax + 16) * 4 * (int64_t)bm_s4((int)Wmax) : 0;
   if (words > 0 && (double)kern[3].grid * (double)words * 4.0 > 8.0 * (double)(1ull << 30)) {
     set_error("bitset engine: out-degree %lld needs too much row scratch", (long long)dmax);
     return PGM_EUNSUPPORTED;
@@ -601,10 +599,8 @@ pgm_status count_kcliques_bitset(Graph& g, Workspace& ws, cudaStream_t s, int k,
       if (b < 3 && lo[b] >= smem_d) continue;  // bucket unused at this shared-memory limit
       if (b == 3 && dmax <= smem_d) continue;
       const Kern& K = kern[b];
-      if (b == 0) bm_block_kernel<256, 256><<<K.grid, K.threads, K.smem, s>>>(B, b);
-      if (b == 1) bm_block_kernel<512, 512><<<K.grid, K.threads, K.smem, s>>>(B, b);
-      if (b == 2) bm_block_kernel<1024, 1024><<<K.grid, K.threads, K.smem, s>>>(B, b);
-      if (b == 3) bm_block_kernel<0, 512><<<K.grid, K.threads, K.smem, s>>>(B, b);
+      void* argv[] = {&B, &b};
+      PGM_TRY_CUDA(cudaLaunchKernel(K.fn, dim3(K.grid), dim3(K.threads), argv, K.smem, s));
       PGM_CHECK_LAUNCH();
     }
   }
