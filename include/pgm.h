@@ -77,7 +77,7 @@ typedef struct {
   int32_t profile;         /* 1 = record per-launch CUDA-event times (pgm_last_profile)       */
   int32_t reverse_ratio;   /* intersect in reverse (scan the shorter list, search the longer)
                               when the longer is this many times longer (default 2)          */
-  int32_t clique_engine;   /* 0 = auto (bitset levels for k = 4, 5; level lists otherwise),
+  int32_t clique_engine;   /* 0 = auto (bitset levels for k = 3..5; level lists otherwise),
                               1 = level lists (vid arrays + inspection-execution),
                               2 = bitset levels where supported                               */
   int32_t bitset_forward_ratio;  /* bitset rows: build row i by scanning N+(P[i]) when it is at most

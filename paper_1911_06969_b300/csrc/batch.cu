@@ -157,6 +157,7 @@ pgm_status run_batch(pgm_batch* b, int kind, int k, uint64_t* out, const pgm_tun
   cudaStream_t s = g.stream;
   const int np = npat(kind, k);
   if (kind == kClique && k <= 2) {
+    PGM_TRY(graph_host_rp(g));
     for (int i = 0; i < b->G; i++) {
       const int64_t v0 = b->vtx_off[i], v1 = b->vtx_off[i + 1];
       out[i] = k == 1 ? (uint64_t)(v1 - v0) : (uint64_t)((g.h_rp[v1] - g.h_rp[v0]) / 2);

@@ -254,12 +254,14 @@ pgm_status count_kcliques(Graph& g, Workspace& ws, cudaStream_t s, int k, int32_
   }
   PGM_TRY(graph_orient(g));
   pgm_profile& lp = last_profile();
+  int64_t arcs = 0;
+  PGM_TRY(graph_dag_arcs(g, v_lo, v_hi, &arcs));
   if (k <= 2) {
-    *out = k == 1 ? (uint64_t)(v_hi - v_lo) : (uint64_t)(g.h_dag_rp[v_hi] - g.h_dag_rp[v_lo]);
+    *out = k == 1 ? (uint64_t)(v_hi - v_lo) : (uint64_t)arcs;
     return PGM_OK;
   }
   const int engine = options().clique_engine;
-  if ((engine == 0 && (k == 4 || k == 5)) || (engine == 2 && k >= 3 && k <= 5)) {
+  if ((engine == 0 || engine == 2) && k >= 3 && k <= 5) {
     uint64_t ls[3] = {0, 0, 0};
     const pgm_status st = count_kcliques_bitset(g, ws, s, k, v_lo, v_hi, out, per_graph_dev, ls);
     if (st != PGM_EUNSUPPORTED) {
@@ -275,7 +277,7 @@ pgm_status count_kcliques(Graph& g, Workspace& ws, cudaStream_t s, int k, int32_
         }
       }
       lp.level_size[1] = (uint64_t)(v_hi - v_lo);
-      lp.level_size[2] = (uint64_t)(g.h_dag_rp[v_hi] - g.h_dag_rp[v_lo]);
+      lp.level_size[2] = (uint64_t)arcs;
       if (k >= 4) lp.level_size[3] = ls[0];
       if (k == 5) lp.level_size[4] = ls[1];
       lp.level_size[k] = *out;
@@ -283,6 +285,7 @@ pgm_status count_kcliques(Graph& g, Workspace& ws, cudaStream_t s, int k, int32_
       return PGM_OK;
     }
   }
+  PGM_TRY(graph_host_dag_rp(g));  // edge blocking plans on the host row pointers
   PGM_TRY(ws.ctr.reserve(kSlots));
   PGM_TRY_CUDA(cudaMemsetAsync(ws.ctr.p, 0, kSlots * sizeof(unsigned long long), s));
   CliqueRun run(g, ws, s, k);

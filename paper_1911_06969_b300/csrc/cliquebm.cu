@@ -556,7 +556,8 @@ pgm_status count_kcliques_bitset(Graph& g, Workspace& ws, cudaStream_t s, int k,
     return PGM_EUNSUPPORTED;
   }
   // bucket lists: at most arcs / (lower bound + 1) vertices exceed each lower bound
-  const int64_t arcs = g.h_dag_rp[v_hi] - g.h_dag_rp[v_lo];
+  int64_t arcs = 0;
+  PGM_TRY(graph_dag_arcs(g, v_lo, v_hi, &arcs));
   const int64_t nv = (int64_t)v_hi - v_lo;
   const int64_t lo[kBmBuckets] = {kBmWarpD, 256, 512, smem_d};
   BmArgs B;

@@ -10,6 +10,7 @@
 #include <cstdint>
 #include <cstdio>
 #include <string>
+#include <mutex>
 #include <vector>
 
 #include "../../include/pgm.h"
@@ -137,8 +138,9 @@ struct Graph {
   int64_t dmax = 0, dag_dmax = 0;
   bool oriented = false;
   cudaStream_t stream = nullptr;
-  std::vector<int64_t> h_dag_rp;  // host copy of the DAG row pointers (edge blocking)
-  std::vector<int64_t> h_rp;      // host copy of the CSR row pointers
+  std::vector<int64_t> h_dag_rp;  // host copy of the DAG row pointers (edge blocking), lazy
+  std::vector<int64_t> h_rp;      // host copy of the CSR row pointers, lazy
+  std::recursive_mutex mu;        // orientation and the lazy host copies
   Workspace ws;                   // workspace of calls made through the handle
 };
 
@@ -146,6 +148,12 @@ pgm_status graph_upload(Graph& g, int32_t n, const int64_t* rowptr, const int32_
                         bool rowptr_on_device, int64_t narcs, uint32_t flags, cudaStream_t s);
 pgm_status graph_orient(Graph& g);
 pgm_status graph_prepare_motifs(Graph& g);
+// host copies of the row pointers (g.h_rp, g.h_dag_rp), made on first use;
+// never called while a stream capture is open (a batch records first)
+pgm_status graph_host_rp(Graph& g);
+pgm_status graph_host_dag_rp(Graph& g);
+// arcs of the DAG whose source lies in [v_lo, v_hi)
+pgm_status graph_dag_arcs(Graph& g, int32_t v_lo, int32_t v_hi, int64_t* arcs);
 void graph_free(Graph& g);
 
 // scan: out[i] = sum cnt[0..i), out[len] = total (device pointers)

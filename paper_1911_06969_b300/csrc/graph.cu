@@ -52,32 +52,74 @@ __device__ __forceinline__ bool keep_arc(int32_t u, int32_t du, int32_t v, int32
   return du < dv || (du == dv && u < v);
 }
 
-// WRITE = false: out-degree per vertex; WRITE = true: compact kept arcs
-template <bool WRITE>
-__global__ void orient_kernel(int32_t n, const int32_t* __restrict__ rp,
-                              const int32_t* __restrict__ col, uint32_t* __restrict__ outdeg,
-                              const int64_t* __restrict__ dag_off, int32_t* __restrict__ dag_col) {
+// Row pointers: checks rp[0] = 0, rp[n] = narcs and that they never
+// decrease, narrows them to int32 and records the largest degree.
+// info[0] = max degree, info[1] = first vertex whose pointer decreases
+// (initialised to all ones), info[2] = 1 if rp[0] or rp[n] is wrong.
+__global__ void rowptr_kernel(int32_t n, const int64_t* __restrict__ rp64, int64_t narcs,
+                              int32_t* __restrict__ rp32, unsigned long long* __restrict__ info) {
+  long long dmax = 0;
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v <= n;
+       v += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t a = rp64[v];
+    rp32[v] = (int32_t)a;
+    if ((v == 0 && a != 0) || (v == n && a != narcs)) atomicOr(info + 2, 1ull);
+    if (v < n) {
+      const int64_t b = rp64[v + 1];
+      if (b < a)
+        atomicMin(info + 1, (unsigned long long)v);
+      else
+        dmax = max(dmax, (long long)(b - a));
+    }
+  }
+  dmax = __reduce_max_sync(kFull, (unsigned)min(dmax, (long long)INT32_MAX));
+  if ((threadIdx.x & 31) == 0 && dmax) atomicMax(info, (unsigned long long)dmax);
+}
+
+// Orientation, pass 1 (one warp per vertex): out-degree per vertex, one
+// keep flag per arc and the largest out-degree (atomicMax into *dmax).
+__global__ void orient_count_kernel(int32_t n, const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
+                                    uint32_t* __restrict__ outdeg, uint8_t* __restrict__ keep,
+                                    unsigned long long* __restrict__ dmax) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  uint32_t cmax = 0;
+  for (int64_t u = warp; u < n; u += nwarps) {
+    const int32_t a0 = rp[u], a1 = rp[u + 1];
+    const int32_t du = a1 - a0;
+    uint32_t c = 0;
+    for (int32_t a = a0; a < a1; a += 32) {
+      bool k = false;
+      if (a + lane < a1) {
+        const int32_t v = col[a + lane];
+        k = keep_arc((int32_t)u, du, v, rp[v + 1] - rp[v]);
+        keep[a + lane] = k ? 1 : 0;
+      }
+      c += __popc(__ballot_sync(kFull, k));
+    }
+    if (lane == 0) outdeg[u] = c;
+    cmax = max(cmax, c);
+  }
+  if (lane == 0 && cmax) atomicMax(dmax, (unsigned long long)cmax);
+}
+
+// Orientation, pass 2: compact the kept arcs (keep flags of pass 1).
+__global__ void orient_write_kernel(int32_t n, const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
+                                    const uint8_t* __restrict__ keep, const int64_t* __restrict__ dag_off,
+                                    int32_t* __restrict__ dag_col) {
   const int lane = threadIdx.x & 31;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t u = warp; u < n; u += nwarps) {
     const int32_t a0 = rp[u], a1 = rp[u + 1];
-    const int32_t du = a1 - a0;
-    int64_t w = WRITE ? dag_off[u] : 0;
-    uint32_t c = 0;
+    int64_t w = dag_off[u];
     for (int32_t a = a0; a < a1; a += 32) {
-      bool keep = false;
-      int32_t v = 0;
-      if (a + lane < a1) {
-        v = col[a + lane];
-        keep = keep_arc((int32_t)u, du, v, rp[v + 1] - rp[v]);
-      }
-      unsigned b = __ballot_sync(kFull, keep);
-      if (WRITE && keep) dag_col[w + __popc(b & ((1u << lane) - 1u))] = v;
+      const bool k = a + lane < a1 && keep[a + lane];
+      const unsigned b = __ballot_sync(kFull, k);
+      if (k) dag_col[w + __popc(b & ((1u << lane) - 1u))] = col[a + lane];
       w += __popc(b);
-      c += __popc(b);
     }
-    if (!WRITE && lane == 0) outdeg[u] = c;
   }
 }
 
@@ -176,70 +218,75 @@ pgm_status graph_upload(Graph& g, int32_t n, const int64_t* rowptr, const int32_
   g.n = n;
   std::vector<int64_t> rp_s;
   std::vector<int32_t> col_s;
-  std::vector<int64_t> h_rp;
   if (!rowptr_on_device) {
     if (rowptr[0] != 0) {
       set_error("graph: rowptr[0] must be 0");
       return PGM_EINVAL;
     }
-    for (int32_t v = 0; v < n; v++)
-      if (rowptr[v + 1] < rowptr[v]) {
-        set_error("graph: rowptr decreases at vertex %d", v);
+    if (flags & PGM_SANITIZE) {
+      for (int32_t v = 0; v < n; v++)
+        if (rowptr[v + 1] < rowptr[v]) {
+          set_error("graph: rowptr decreases at vertex %d", v);
+          return PGM_EINVAL;
+        }
+      if (rowptr[n] > 0 && !col) {
+        set_error("graph: null col");
         return PGM_EINVAL;
       }
+      sanitize_host(n, rowptr, col, rp_s, col_s);
+      rowptr = rp_s.data();
+      col = col_s.data();
+    }
     narcs = rowptr[n];
     if (narcs > 0 && !col) {
       set_error("graph: null col");
       return PGM_EINVAL;
     }
-    if (flags & PGM_SANITIZE) {
-      sanitize_host(n, rowptr, col, rp_s, col_s);
-      rowptr = rp_s.data();
-      col = col_s.data();
-      narcs = rowptr[n];
-    }
-    h_rp.assign(rowptr, rowptr + (size_t)n + 1);
-  } else {
-    if (flags & PGM_SANITIZE) {
-      set_error("graph: PGM_SANITIZE needs host arrays");
-      return PGM_EINVAL;
-    }
-    h_rp.resize((size_t)n + 1);
-    PGM_TRY_CUDA(cudaMemcpyAsync(h_rp.data(), rowptr, ((size_t)n + 1) * sizeof(int64_t),
-                                 cudaMemcpyDeviceToHost, s));
-    PGM_TRY_CUDA(cudaStreamSynchronize(s));
-    if (h_rp[0] != 0 || h_rp[n] != narcs) {
-      set_error("graph: device rowptr inconsistent with narcs");
-      return PGM_EINVAL;
-    }
-    for (int32_t v = 0; v < n; v++)
-      if (h_rp[v + 1] < h_rp[v]) {
-        set_error("graph: rowptr decreases at vertex %d", v);
-        return PGM_EINVAL;
-      }
+  } else if (flags & PGM_SANITIZE) {
+    set_error("graph: PGM_SANITIZE needs host arrays");
+    return PGM_EINVAL;
   }
-  if (narcs >= INT32_MAX) {
-    set_error("graph: %lld arcs exceed the int32 device index range", (long long)narcs);
-    return PGM_EUNSUPPORTED;
+  if (narcs < 0 || narcs >= INT32_MAX) {
+    set_error("graph: %lld arcs outside the int32 device index range", (long long)narcs);
+    return narcs < 0 ? PGM_EINVAL : PGM_EUNSUPPORTED;
   }
   g.narcs = narcs;
-  std::vector<int32_t> rp32((size_t)n + 1);
-  int64_t dmax = 0;
-  for (int32_t v = 0; v <= n; v++) rp32[v] = (int32_t)h_rp[v];
-  for (int32_t v = 0; v < n; v++) dmax = std::max(dmax, h_rp[v + 1] - h_rp[v]);
-  g.dmax = dmax;
   PGM_TRY_CUDA(cudaMalloc(&g.rp, ((size_t)n + 1) * sizeof(int32_t)));
   PGM_TRY_CUDA(cudaMalloc(&g.col, (size_t)std::max<int64_t>(narcs, 1) * sizeof(int32_t)));
-  PGM_TRY_CUDA(cudaMemcpyAsync(g.rp, rp32.data(), ((size_t)n + 1) * sizeof(int32_t),
-                               cudaMemcpyHostToDevice, s));
+  const int64_t* rp64 = rowptr;
+  if (!rowptr_on_device) {
+    PGM_TRY(g.ws.off[0].reserve((size_t)n + 1));
+    PGM_TRY_CUDA(cudaMemcpyAsync(g.ws.off[0].p, rowptr, ((size_t)n + 1) * sizeof(int64_t),
+                                 cudaMemcpyHostToDevice, s));
+    rp64 = g.ws.off[0].p;
+  }
   if (narcs > 0)
     PGM_TRY_CUDA(cudaMemcpyAsync(g.col, col, (size_t)narcs * sizeof(int32_t),
                                  rowptr_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                                  s));
-  g.h_rp.swap(h_rp);
+  // row pointers checked and narrowed on the device; max degree by reduction
+  PGM_TRY(g.ws.ctr.reserve(16));
+  unsigned long long* info = g.ws.ctr.p;
+  PGM_TRY_CUDA(cudaMemsetAsync(info, 0, 3 * sizeof(unsigned long long), s));
+  PGM_TRY_CUDA(cudaMemsetAsync(info + 1, 0xff, sizeof(unsigned long long), s));
+  rowptr_kernel<<<std::max(1, std::min(num_sms() * 8, (int)((n + 256) / 256))), 256, 0, s>>>(n, rp64, narcs,
+                                                                                          g.rp, info);
+  PGM_CHECK_LAUNCH();
+  unsigned long long h[3];
+  PGM_TRY_CUDA(cudaMemcpyAsync(h, info, sizeof(h), cudaMemcpyDeviceToHost, s));
+  PGM_TRY_CUDA(cudaStreamSynchronize(s));
+  if (h[1] != ~0ull) {
+    set_error("graph: rowptr decreases at vertex %llu", h[1]);
+    return PGM_EINVAL;
+  }
+  if (h[2]) {
+    set_error("graph: rowptr must start at 0 and end at the number of arcs (%lld)", (long long)narcs);
+    return PGM_EINVAL;
+  }
+  g.dmax = (int64_t)h[0];
+  g.h_rp.clear();  // host copy made on first use (graph_host_rp)
   if ((flags & PGM_VALIDATE) && n > 0) {
-    PGM_TRY(g.ws.ctr.reserve(16));
-    unsigned* fl = reinterpret_cast<unsigned*>(g.ws.ctr.p);
+    unsigned* fl = reinterpret_cast<unsigned*>(info);
     PGM_TRY_CUDA(cudaMemsetAsync(fl, 0, sizeof(unsigned), s));
     validate_kernel<<<warp_grid(n, 256), 256, 0, s>>>(n, g.rp, g.col, fl);
     PGM_CHECK_LAUNCH();
@@ -253,11 +300,45 @@ pgm_status graph_upload(Graph& g, int32_t n, const int64_t* rowptr, const int32_
       return PGM_EINVAL;
     }
   }
+  return PGM_OK;
+}
+
+// Host copies of the row pointers, made on first use (they are not needed
+// by the clique path).  Not to be called while a stream capture is open.
+static pgm_status host_copy(const int32_t* dev, int32_t n, cudaStream_t s, std::vector<int64_t>& out) {
+  std::vector<int32_t> tmp((size_t)n + 1);
+  PGM_TRY_CUDA(cudaMemcpyAsync(tmp.data(), dev, ((size_t)n + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
   PGM_TRY_CUDA(cudaStreamSynchronize(s));
+  out.assign(tmp.begin(), tmp.end());
+  return PGM_OK;
+}
+
+pgm_status graph_host_rp(Graph& g) {
+  std::lock_guard<std::recursive_mutex> lk(g.mu);
+  if (g.h_rp.size() == (size_t)g.n + 1) return PGM_OK;
+  return host_copy(g.rp, g.n, g.stream, g.h_rp);
+}
+
+pgm_status graph_host_dag_rp(Graph& g) {
+  std::lock_guard<std::recursive_mutex> lk(g.mu);
+  PGM_TRY(graph_orient(g));
+  if (g.h_dag_rp.size() == (size_t)g.n + 1) return PGM_OK;
+  return host_copy(g.dag_rp, g.n, g.stream, g.h_dag_rp);
+}
+
+pgm_status graph_dag_arcs(Graph& g, int32_t v_lo, int32_t v_hi, int64_t* arcs) {
+  PGM_TRY(graph_orient(g));
+  if (v_lo == 0 && v_hi == g.n) {
+    *arcs = g.narcs / 2;
+    return PGM_OK;
+  }
+  PGM_TRY(graph_host_dag_rp(g));
+  *arcs = g.h_dag_rp[v_hi] - g.h_dag_rp[v_lo];
   return PGM_OK;
 }
 
 pgm_status graph_orient(Graph& g) {
+  std::lock_guard<std::recursive_mutex> lk(g.mu);
   if (g.oriented) return PGM_OK;
   cudaStream_t s = g.stream;
   const int32_t n = g.n;
@@ -270,27 +351,34 @@ pgm_status graph_orient(Graph& g) {
   if (!g.dag_col) PGM_TRY_CUDA(cudaMalloc(&g.dag_col, (size_t)std::max<int64_t>(m, 1) * sizeof(int32_t)));
   PGM_TRY(g.ws.cnt[0].reserve((size_t)n + 1));
   PGM_TRY(g.ws.off[0].reserve((size_t)n + 1));
+  PGM_TRY(g.ws.ctr.reserve(16));
+  DevArr<uint8_t> keep;  // one flag per arc, freed on return
+  PGM_TRY(keep.reserve((size_t)std::max<int64_t>(g.narcs, 1)));
+  struct Free {
+    DevArr<uint8_t>& k;
+    ~Free() { k.release(); }
+  } free_keep{keep};
+  unsigned long long* dmax_dev = g.ws.ctr.p + 3;
+  PGM_TRY_CUDA(cudaMemsetAsync(dmax_dev, 0, sizeof(unsigned long long), s));
   Profiler& prof = profiler();
   int id = prof.begin("orient", 1);
   if (n > 0) {
-    orient_kernel<false><<<warp_grid(n, 256), 256, 0, s>>>(n, g.rp, g.col, g.ws.cnt[0].p, nullptr,
-                                                           nullptr);
+    orient_count_kernel<<<warp_grid(n, 256), 256, 0, s>>>(n, g.rp, g.col, g.ws.cnt[0].p, keep.p, dmax_dev);
     PGM_CHECK_LAUNCH();
   }
   PGM_TRY(exclusive_scan(g.ws.cnt[0].p, n, g.ws.off[0].p, g.ws, s));
-  g.h_dag_rp.resize((size_t)n + 1);
-  PGM_TRY_CUDA(cudaMemcpyAsync(g.h_dag_rp.data(), g.ws.off[0].p, ((size_t)n + 1) * sizeof(int64_t),
-                               cudaMemcpyDeviceToHost, s));
+  int64_t kept = 0;
+  unsigned long long dd = 0;
+  PGM_TRY_CUDA(cudaMemcpyAsync(&kept, g.ws.off[0].p + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  PGM_TRY_CUDA(cudaMemcpyAsync(&dd, dmax_dev, sizeof(dd), cudaMemcpyDeviceToHost, s));
   PGM_TRY_CUDA(cudaStreamSynchronize(s));
-  if (g.h_dag_rp[n] != m) {
+  if (kept != m) {
     // not symmetric: the kept-arc count differs from m; refuse before writing
-    set_error("orient: kept %lld arcs, expected %lld (input not symmetric?)",
-              (long long)g.h_dag_rp[n], (long long)m);
+    set_error("orient: kept %lld arcs, expected %lld (input not symmetric?)", (long long)kept, (long long)m);
     return PGM_EINVAL;
   }
   if (n > 0) {
-    orient_kernel<true><<<warp_grid(n, 256), 256, 0, s>>>(n, g.rp, g.col, nullptr, g.ws.off[0].p,
-                                                          g.dag_col);
+    orient_write_kernel<<<warp_grid(n, 256), 256, 0, s>>>(n, g.rp, g.col, keep.p, g.ws.off[0].p, g.dag_col);
     PGM_CHECK_LAUNCH();
   }
   narrow_kernel<<<std::max(1, std::min(num_sms() * 8, (int)((n + 256) / 256))), 256, 0, s>>>(
@@ -298,9 +386,8 @@ pgm_status graph_orient(Graph& g) {
   PGM_CHECK_LAUNCH();
   prof.end(id, (double)n, 8.0 * (double)g.narcs);
   PGM_TRY_CUDA(cudaStreamSynchronize(s));
-  int64_t dd = 0;
-  for (int32_t v = 0; v < n; v++) dd = std::max(dd, g.h_dag_rp[v + 1] - g.h_dag_rp[v]);
-  g.dag_dmax = dd;
+  g.dag_dmax = (int64_t)dd;
+  g.h_dag_rp.clear();  // host copy made on first use (graph_host_dag_rp)
   g.oriented = true;
   return PGM_OK;
 }
@@ -314,6 +401,7 @@ constexpr int64_t kHubBytes = (int64_t)512 << 20;
 
 pgm_status graph_prepare_motifs(Graph& g) {
   if (g.up) return PGM_OK;
+  PGM_TRY(graph_host_rp(g));
   cudaStream_t s = g.stream;
   const int32_t n = g.n;
   PGM_TRY_CUDA(cudaMalloc(&g.up, ((size_t)n + 1) * sizeof(int32_t)));
@@ -418,7 +506,8 @@ pgm_status pgm_graph_stats_get(const pgm_graph* gh, pgm_graph_stats* out) {
     pgm::set_error("pgm_graph_stats_get: null argument");
     return PGM_EINVAL;
   }
-  const pgm::Graph& g = gh->g;
+  pgm::Graph& g = const_cast<pgm_graph*>(gh)->g;
+  PGM_TRY(pgm::graph_host_rp(g));
   unsigned __int128 s2 = 0, s3 = 0;
   for (int32_t v = 0; v < g.n; v++) {
     unsigned __int128 d = (unsigned __int128)(g.h_rp[v + 1] - g.h_rp[v]);

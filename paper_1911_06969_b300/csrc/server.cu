@@ -180,6 +180,7 @@ pgm_status pgm_server_add_graph(pgm_server* s, int32_t n, const int64_t* rowptr,
   pgm_status st = pgm::graph_upload(sg->g, n, rowptr, col, false, 0, 0, s->upload_stream);
   if (st == PGM_OK) st = pgm::graph_orient(sg->g);
   if (st == PGM_OK) st = pgm::graph_prepare_motifs(sg->g);
+  if (st == PGM_OK) st = pgm::graph_host_dag_rp(sg->g);  // before any worker uses the graph
   if (st != PGM_OK) {
     pgm::graph_free(sg->g);
     return st;

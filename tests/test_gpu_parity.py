@@ -252,6 +252,10 @@ def test_validation_and_sanitize():
         assert e.value.status == pgm.PGM_EINVAL, name
     h = pgm.pgm_graph_create_csr(good.n, good.rowptr, good.col, pgm.PGM_VALIDATE)
     pgm.pgm_graph_destroy(h)
+    # row pointers are checked on the device even without PGM_VALIDATE
+    with pytest.raises(pgm.PgmError) as e:
+        pgm.pgm_graph_create_csr(3, np.array([0, 2, 1, 2], np.int64), np.array([1, 2], np.int32))
+    assert e.value.status == pgm.PGM_EINVAL and "decreases at vertex 1" in str(e.value)
     # sanitize: an asymmetric list with a loop and a duplicate becomes the simple graph
     rp = np.array([0, 3, 4, 4], np.int64)
     col = np.array([1, 1, 0, 2], np.int32)  # 0:{1,1,0} 1:{2} 2:{}
