@@ -396,7 +396,7 @@ pgm_status graph_orient(Graph& g) {
 // src[] (source vertex of each arc) and adjacency bitmaps of the vertices
 // of degree >= kHubDegree (highest degrees first, at most kHubBytes), used
 // for O(1) membership tests against hub adjacency lists.
-constexpr int64_t kHubDegree = 1024;
+constexpr int64_t kHubDegree = 512;  // longer lists than the default staging capacity
 constexpr int64_t kHubBytes = (int64_t)512 << 20;
 
 pgm_status graph_prepare_motifs(Graph& g) {

@@ -332,22 +332,49 @@ __device__ __forceinline__ void add_c_region(long long (&c)[6], int a02, int a12
   }
 }
 
+// Per-warp filter of the last level: one-hash bitmap over A u B (at most
+// kMFilterW words); a clear bit proves that w is in neither list.
+constexpr int kMFilterW = 256;
+
+__device__ __forceinline__ uint32_t mf_hash(int32_t x, int shift) {
+  return ((uint32_t)x * 0x9E3779B1u) >> shift;
+}
+
+// Shared memory of motif_l3_edge per warp, in ints: A, B, I staging,
+// filter, candidate queue (64 vertices + 64 child lanes), 4 region
+// counters per child of the current batch of 32.
+__host__ __device__ constexpr int64_t ml3_warp_ints(int cap) { return 3LL * cap + kMFilterW + 128 + 128; }
+
 // One level-2 edge (v0, v1) per warp at a time, taken from a device queue
 // over arcs, so heavy edges of hub vertices spread over the whole GPU.
 // A = N(v0) & (v0, inf), B = N(v1) & (v0, inf) are staged in shared memory
 // when short (else read in place, with hub bitmaps for membership);
-// I = A & B is built once per edge for the rank queries.  For each child
-// (v2, memo) the candidates adjacent to v2 are enumerated either forward
-// (scan N(v2), look up A and B) or in reverse when N(v2) is much longer
-// than A and B (scan A and B, look up N(v2)); the candidates adjacent only
-// to v2 are then its count above v0 minus the ones seen in A or B.
-__global__ void __launch_bounds__(512) motif_l3_edge(MotifArgs P) {
+// I = A & B is built once per edge for the rank queries, and a bitmap
+// filter over A u B once per edge for the scans.
+//
+// For each child (v2, memo), 32 children at a time (one per lane): the
+// candidates not adjacent to v2 are counted by rank queries on A, B and I;
+// the candidates adjacent to v2 (w in N(v2), w > v0, w != v1) are first
+// all counted as "adjacent to v2 only" (a rank query on N(v2)), then the
+// ones that are also in A or B are moved to their regions.  Those are found
+// either forward -- scan N(v2) above v0, keep the elements that pass the
+// filter, queue them and test them exactly in A and B 32 at a time -- or in
+// reverse when N(v2) is much longer than A and B (scan A and B, test each
+// element in N(v2)).
+constexpr int kML3Threads = 256;  // block size of the last level (at most)
+
+__global__ void __launch_bounds__(kML3Threads, 3) motif_l3_edge(MotifArgs P) {
   extern __shared__ int32_t smem[];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const unsigned lt = (1u << lane) - 1u;
   const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  int32_t* Abuf = smem + (int64_t)wid * 3 * P.cap;
+  int32_t* Abuf = smem + (int64_t)wid * ml3_warp_ints(P.cap);
   int32_t* Bbuf = Abuf + P.cap;
   int32_t* Ismem = Bbuf + P.cap;
+  uint32_t* F = reinterpret_cast<uint32_t*>(Ismem + P.cap);
+  int32_t* Qw = reinterpret_cast<int32_t*>(F + kMFilterW);
+  int32_t* Qq = Qw + 64;
+  int32_t* Cnt = Qq + 64;  // Cnt[4 * q + r]: region counters of child lane q
   int32_t* Iglob = P.scratch + gw * P.scratch_stride;
   long long c[6] = {0, 0, 0, 0, 0, 0};
   unsigned long long seen = 0;
@@ -395,7 +422,16 @@ __global__ void __launch_bounds__(512) motif_l3_edge(MotifArgs P) {
       } else {
         B = P.col + r0 + bstart;
       }
+      // filter over A u B: 32 * fw bits
+      int fw = 32;
+      while (fw < s + nb && fw < kMFilterW) fw <<= 1;
+      const int fshift = 32 - (__ffs(fw) - 1) - 5;
+      for (int i = lane; i < fw; i += 32) F[i] = 0u;
       __syncwarp();
+      for (int i = lane; i < s + nb; i += 32) {
+        const uint32_t h = mf_hash(i < s ? A[i] : B[i - s], fshift);
+        atomicOr(F + (h >> 5), 1u << (h & 31));
+      }
       // I = A & B, sorted: scan the shorter list, test membership in the other
       int32_t* I = min(s, nb) <= P.cap ? Ismem : Iglob;
       int ni = 0;
@@ -414,7 +450,7 @@ __global__ void __launch_bounds__(512) motif_l3_edge(MotifArgs P) {
             in = member(Y, ny, hy, P, x);
           }
           const unsigned bal = __ballot_sync(kFull, in);
-          if (in) I[ni + __popc(bal & ((1u << lane) - 1u))] = x;
+          if (in) I[ni + __popc(bal & lt)] = x;
           ni += __popc(bal);
         }
       }
@@ -424,13 +460,13 @@ __global__ void __launch_bounds__(512) motif_l3_edge(MotifArgs P) {
       for (int64_t c0 = cb; c0 < ce; c0 += 32) {
         const int64_t ci = c0 + lane;
         const bool valid = ci < ce;
-        int32_t v2 = 0, a0 = 0, d2 = 0, len = 0;
-        int a02 = 0, a12 = 0, rev = 0, hC = -1;
+        int32_t v2 = 0, a0 = 0, d2 = 0, len = 0, start = 0;
+        int flags = 0, hC = -1;  // flags: bit 0 a02, bit 1 a12, bit 2 reverse
         if (valid) {
           const uint32_t e = P.l3[ci];
           v2 = (int32_t)(e & kVidMask);
-          a02 = (e & kA02) ? 1 : 0;
-          a12 = (e & kA12) ? 1 : 0;
+          const int a02 = (e & kA02) ? 1 : 0;
+          const int a12 = (e & kA12) ? 1 : 0;
           a0 = P.rp[v2];
           d2 = P.rp[v2 + 1] - a0;
           hC = P.hub_idx[v2];
@@ -446,62 +482,162 @@ __global__ void __launch_bounds__(512) motif_l3_edge(MotifArgs P) {
             const int ib = lower_bound_dev(B, nb, v2 + 1);
             add_pat<6>(c, pattern4(0, 1, 2), (long long)(nb - ib) - I_gt2);  // B only, w > v2
           }
-          rev = (long long)d2 > (long long)P.rev_ratio * (long long)(s + nb);
+          // every w of N(v2) above v0 except v1 starts as "adjacent to v2 only"
+          const int lo = lower_bound_dev(P.col + a0, d2, v0 + 1);
+          add_pat<6>(c, pattern4(a02, a12, 4), (long long)(d2 - lo - a12));
+          const int rev = (long long)(d2 - lo) > (long long)P.rev_ratio * (long long)(s + nb);
+          flags = a02 | (a12 << 1) | (rev << 2);
           if (rev) {
-            // every candidate of N(v2) above v0 except v1 starts as "adjacent to v2 only";
-            // the reverse scan moves the ones also in A or B to their regions
-            const int lo = lower_bound_dev(P.col + a0, d2, v0 + 1);
-            add_pat<6>(c, pattern4(a02, a12, 4), (long long)(d2 - lo - a12));
             len = s + nb;
           } else {
-            len = d2;
+            len = d2 - lo;
+            start = a0 + lo;
           }
         }
         seen += (unsigned long long)len;
         const int incl = warp_inclusive_scan(len, lane);
         const int total = __shfl_sync(kFull, incl, 31);
         const int excl = incl - len;
-        for (int base = 0; base < total; base += 32) {
-          const int t = base + lane;
-          const bool active = t < total;
-          const int q = min(warp_owner(incl, t), 31);
-          const int aq = __shfl_sync(kFull, a0, q);
-          const int eq = __shfl_sync(kFull, excl, q);
+        int qn = 0;  // queued forward candidates (warp-uniform)
+        // region counters of this lane's child: [0] queued elements found in A or B,
+        // [1] in A only and above v2, [2] in A and B and above v2, [3] in B only
+        // (and above v2 when the child is not adjacent to v0)
+#pragma unroll
+        for (int r = 0; r < 4; r++) Cnt[4 * lane + r] = 0;
+        __syncwarp();
+        // exact test of queued candidates w (child lane q, non-decreasing over the
+        // lanes); the counts of each run of equal q are added by its first lane
+        auto process = [&](int32_t w, int q, bool ok) {
+          const int fq = __shfl_sync(kFull, flags, q);
           const int32_t v2q = __shfl_sync(kFull, v2, q);
-          const int a02q = __shfl_sync(kFull, a02, q);
-          const int a12q = __shfl_sync(kFull, a12, q);
-          const int revq = __shfl_sync(kFull, rev, q);
-          const int d2q = __shfl_sync(kFull, d2, q);
-          const int hCq = __shfl_sync(kFull, hC, q);
-          if (!active) continue;
-          const int tq = t - eq;
-          if (!revq) {
-            const int32_t w = P.col[aq + tq];
-            if (w > v0 && w != v1) {
-              const int ia = member(A, s, hA, P, w) ? 1 : 0;
-              const int ib = member(B, nb, hB, P, w) ? 1 : 0;
-              add_c_region(c, a02q, a12q, ia, ib, w, v2q);
+          bool hit = false, r1 = false, r2 = false, r3 = false;
+          if (ok) {
+            const bool ia = member(A, s, hA, P, w);
+            const bool ib = member(B, nb, hB, P, w);
+            const bool gt = w > v2q;
+            hit = ia || ib;
+            r1 = ia && !ib && gt;
+            r2 = ia && ib && gt;
+            r3 = !ia && ib && ((fq & 1) || gt);
+          }
+          const int qq = ok ? q : 32;
+          const int qprev = __shfl_up_sync(kFull, qq, 1);
+          const bool head = ok && (lane == 0 || qprev != qq);
+          const unsigned heads = __ballot_sync(kFull, head) | ~__ballot_sync(kFull, ok);
+          const unsigned bh = __ballot_sync(kFull, hit), b1 = __ballot_sync(kFull, r1);
+          const unsigned b2 = __ballot_sync(kFull, r2), b3 = __ballot_sync(kFull, r3);
+          if (head) {
+            const unsigned after = heads & ~((2u << lane) - 1u);  // heads (or unused lanes) after this one
+            const unsigned upto = after ? ((1u << (__ffs(after) - 1)) - 1u) : 0xffffffffu;
+            const unsigned seg = upto & ~lt;
+            Cnt[4 * q + 0] += __popc(bh & seg);
+            Cnt[4 * q + 1] += __popc(b1 & seg);
+            Cnt[4 * q + 2] += __popc(b2 & seg);
+            Cnt[4 * q + 3] += __popc(b3 & seg);
+          }
+        };
+        // the flattened (child, element) slots, kU chunks of 32 at a time: the
+        // loads of all chunks are issued before their elements are tested
+        constexpr int kU = 4;
+        for (int base = 0; base < total; base += 32 * kU) {
+          int32_t wv[kU];
+          int qv[kU];
+          bool anyrev = false;
+#pragma unroll
+          for (int r = 0; r < kU; r++) {
+            const int t = base + r * 32 + lane;
+            const bool active = t < total;
+            const int q = min(warp_owner(incl, t), 31);
+            const int eq = __shfl_sync(kFull, excl, q);
+            const int fq = __shfl_sync(kFull, flags, q);
+            const int stq = __shfl_sync(kFull, start, q);
+            wv[r] = (active && !(fq & 4)) ? P.col[stq + t - eq] : -1;
+            qv[r] = q;
+            anyrev = anyrev || (active && (fq & 4));
+          }
+#pragma unroll
+          for (int r = 0; r < kU; r++) {
+            const int32_t w = wv[r];
+            bool cand = false;
+            if (w >= 0 && w != v1) {
+              const uint32_t h = mf_hash(w, fshift);
+              cand = (F[h >> 5] >> (h & 31)) & 1u;
             }
-          } else {
-            int32_t w;
-            int ia, ib;
-            if (tq < s) {
-              w = A[tq];
-              ia = 1;
-              if (w == v1 || w == v2q) continue;
-              ib = member(B, nb, hB, P, w) ? 1 : 0;
-            } else {
-              w = B[tq - s];
-              if (w == v2q || member(A, s, hA, P, w)) continue;  // A's copy is counted above
-              ia = 0;
-              ib = 1;
+            const unsigned bal = __ballot_sync(kFull, cand);
+            if (cand) {
+              const int pos = qn + __popc(bal & lt);
+              Qw[pos] = w;
+              Qq[pos] = qv[r];
             }
-            if (member(P.col + aq, d2q, hCq, P, w)) {
-              add_pat<6>(c, pattern4(a02q, a12q, 4), -1);  // not adjacent to v2 only
-              add_c_region(c, a02q, a12q, ia, ib, w, v2q);
+            qn += __popc(bal);
+            if (qn >= 32) {
+              __syncwarp();
+              process(Qw[lane], Qq[lane], true);
+              __syncwarp();
+              if (lane < qn - 32) {
+                Qw[lane] = Qw[lane + 32];
+                Qq[lane] = Qq[lane + 32];
+              }
+              qn -= 32;
+              __syncwarp();
+            }
+          }
+          if (__any_sync(kFull, anyrev)) {
+            // reverse: scan A and B, test each element in N(v2)
+            for (int r = 0; r < kU; r++) {
+              const int t = base + r * 32 + lane;
+              const bool active = t < total;
+              const int q = min(warp_owner(incl, t), 31);
+              const int eq = __shfl_sync(kFull, excl, q);
+              const int fq = __shfl_sync(kFull, flags, q);
+              const int aq = __shfl_sync(kFull, a0, q);
+              const int32_t v2q = __shfl_sync(kFull, v2, q);
+              const int d2q = __shfl_sync(kFull, d2, q);
+              const int hCq = __shfl_sync(kFull, hC, q);
+              if (active && (fq & 4)) {
+                const int tq = t - eq;
+                const int a02q = fq & 1, a12q = (fq >> 1) & 1;
+                int32_t x;
+                int ia, ib;
+                bool skip = false;
+                if (tq < s) {
+                  x = A[tq];
+                  ia = 1;
+                  skip = x == v1 || x == v2q;
+                  ib = skip ? 0 : (member(B, nb, hB, P, x) ? 1 : 0);
+                } else {
+                  x = B[tq - s];
+                  ia = 0;
+                  ib = 1;
+                  skip = x == v2q || member(A, s, hA, P, x);  // A's copy is counted above
+                }
+                if (!skip && member(P.col + aq, d2q, hCq, P, x)) {
+                  add_pat<6>(c, pattern4(a02q, a12q, 4), -1);  // not adjacent to v2 only
+                  add_c_region(c, a02q, a12q, ia, ib, x, v2q);
+                }
+              }
             }
           }
         }
+        __syncwarp();
+        process(Qw[lane], Qq[lane], lane < qn);
+        __syncwarp();
+        if (valid && !(flags & 4)) {
+          const int a12 = (flags >> 1) & 1;
+          add_pat<6>(c, pattern4(flags & 1, a12, 4), -(long long)Cnt[4 * lane]);
+          if (flags & 1) {
+            add_pat<6>(c, pattern4(1, a12, 5), Cnt[4 * lane + 1]);
+            add_pat<6>(c, pattern4(1, a12, 1), -(long long)Cnt[4 * lane + 1]);
+            add_pat<6>(c, pattern4(1, a12, 7), Cnt[4 * lane + 2]);
+            add_pat<6>(c, pattern4(1, a12, 3), -(long long)Cnt[4 * lane + 2]);
+            add_pat<6>(c, pattern4(1, a12, 6), Cnt[4 * lane + 3]);
+            add_pat<6>(c, pattern4(1, a12, 2), -(long long)Cnt[4 * lane + 3]);
+          } else {
+            add_pat<6>(c, pattern4(0, 1, 6), Cnt[4 * lane + 3]);
+            add_pat<6>(c, pattern4(0, 1, 2), -(long long)Cnt[4 * lane + 3]);
+          }
+        }
+        __syncwarp();
       }
     }
   }
@@ -584,9 +720,10 @@ struct MotifRun {
     P.hub_bits = g.hub_bits;
     P.hub_words = g.hub_words;
     P.rev_ratio = o.reverse_ratio;
-    const int threads = o.block_threads;
-    const size_t wsmem = (size_t)(threads / 32) * 3 * cap * sizeof(int32_t);
-    PGM_TRY(smem_attr((const void*)motif_l3_edge, 200 * 1024));
+    const int threads = std::min(o.block_threads, kML3Threads);
+    // at most 16384 staged ints per block (option check) + filter, queue, counters: < 227 KB
+    const size_t wsmem = (size_t)(threads / 32) * ml3_warp_ints(cap) * sizeof(int32_t);
+    PGM_TRY(smem_attr((const void*)motif_l3_edge, (int)std::max<size_t>(wsmem, 200 * 1024)));
     int grid = grid_for((const void*)motif_l3_edge, threads, wsmem);
     const int64_t na = P.arc_hi - P.arc_lo;
     const int64_t blocks_needed = ((na + kEdgeGrab - 1) / kEdgeGrab + threads / 32 - 1) / (threads / 32);
