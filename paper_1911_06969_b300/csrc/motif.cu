@@ -117,6 +117,15 @@ __device__ __forceinline__ void add_pat(long long (&c)[N], int p, long long d) {
   for (int i = 0; i < N; i++) c[i] += (i == p) ? d : 0;
 }
 
+// Membership of w in a sorted list, or by one bit of a hub's adjacency
+// bitmap when the list's owner is a hub (hb >= 0).  Callers only ask about
+// w above the list's lower threshold, so the bitmap of the full adjacency
+// list answers for the thresholded list too.
+__device__ __forceinline__ bool member(const int32_t* L, int len, int hb, const MotifArgs& P, int32_t w) {
+  if (hb >= 0) return (P.hub_bits[(int64_t)hb * P.hub_words + (w >> 5)] >> (w & 31)) & 1u;
+  return len > 0 && w >= L[0] && w <= L[len - 1] && contains_dev(L, len, w);
+}
+
 // ------------------------------------------------------ level 2 -> 3 / 3-motif
 // Entries j0..j0+31 of v0's segment A (length s).  For entry j (v1 = A[j])
 // scan N(v1): x > v0 and not in A -> f2=1 child; x in A and x > v1 -> the
@@ -206,8 +215,102 @@ __device__ __forceinline__ void l2_batch(const MotifArgs& P, const int32_t* A, i
   }
 }
 
+// Counting modes (3-motif sum, level-3 inspection) need only the sizes of
+// the intersections of A (v0's segment) with B_j = N(A[j]) & (v0, inf):
+// for entry j (v1 = A[j]) the children are the f2=0 block A[j+1..s) and the
+// f2=1 block B_j \ A; among the f2=0 children, those in B_j (above v1) are
+// triangles.  Each intersection scans the shorter of A and B_j and tests its
+// elements in the other (staged list, hub bitmap or binary search).
 template <int MODE>
-__global__ void __launch_bounds__(512) motif_l2_warp(MotifArgs P) {
+__device__ __forceinline__ void l2_count_batch(const MotifArgs& P, const int32_t* A, int s, int hA, int j0,
+                                               int32_t v0, int64_t arc0, int lane, uint32_t* wcnt,
+                                               long long (&c)[2], unsigned long long& seen) {
+  const int j = j0 + lane;
+  const bool valid = j < s;
+  int32_t v1 = 0, r1 = 0, d1 = 0, b0 = 0, nbj = 0, len = 0, hv1 = -1, scanB = 0;
+  if (valid) {
+    v1 = A[j];
+    r1 = P.rp[v1];
+    d1 = P.rp[v1 + 1] - r1;
+    const int bs = lower_bound_dev(P.col + r1, d1, v0 + 1);
+    b0 = r1 + bs;
+    nbj = d1 - bs;
+    hv1 = P.hub_idx[v1];
+    scanB = nbj <= s;
+    len = scanB ? nbj : s;
+  }
+  seen += (unsigned long long)len;
+  if (MODE == mSum && valid) c[0] += (long long)(s - j - 1) + nbj;  // all children start as wedges
+  const int incl = warp_inclusive_scan(len, lane);
+  const int total = __shfl_sync(kFull, incl, 31);
+  const int excl = incl - len;
+  if (MODE == mCount) {
+    wcnt[lane] = 0;
+    __syncwarp();
+  }
+  for (int base = 0; base < total; base += 32) {
+    const int t = base + lane;
+    const bool active = t < total;
+    const int q = min(warp_owner(incl, t), 31);
+    const int eq = __shfl_sync(kFull, excl, q);
+    const int sq = __shfl_sync(kFull, scanB, q);
+    const int32_t b0q = __shfl_sync(kFull, b0, q);
+    const int32_t r1q = __shfl_sync(kFull, r1, q);
+    const int d1q = __shfl_sync(kFull, d1, q);
+    const int hq = __shfl_sync(kFull, hv1, q);
+    const int32_t v1q = __shfl_sync(kFull, v1, q);
+    bool in = false;
+    int32_t x = 0;
+    if (active) {
+      const int idx = t - eq;
+      if (sq) {
+        x = P.col[b0q + idx];
+        in = member(A, s, hA, P, x);
+      } else {
+        x = A[idx];
+        in = member(P.col + r1q, d1q, hq, P, x);
+      }
+    }
+    if (MODE == mSum) {
+      if (in) {
+        c[0] -= 1;  // in A: not an f2=1 child
+        if (x > v1q) {
+          c[0] -= 1;  // the f2=0 child x is a triangle
+          c[1] += 1;
+        }
+      }
+    } else {
+      const unsigned b = __ballot_sync(kFull, in);
+      const int first = max(eq - base, 0);
+      const unsigned from_first = ~((1u << first) - 1u);
+      const unsigned upto_me = lane == 31 ? kFull : ((2u << lane) - 1u);
+      const int qn = __shfl_down_sync(kFull, q, 1);
+      const bool last = active && (lane == 31 || t + 1 >= total || qn != q);
+      __syncwarp();
+      if (last) wcnt[q] += __popc(b & from_first & upto_me);
+      __syncwarp();
+    }
+  }
+  if (MODE == mCount) {
+    if (valid) P.cnt[arc0 + j] = (uint32_t)(s - j - 1) + (uint32_t)nbj - wcnt[lane];
+    __syncwarp();
+  }
+}
+
+// Level-2 batch: counting modes by intersection sizes, the write mode by a
+// full scan of each B_j (it writes the children).
+template <int MODE>
+__device__ __forceinline__ void l2_any_batch(const MotifArgs& P, const int32_t* A, int s, int hA, int j0,
+                                             int32_t v0, int64_t arc0, int lane, uint32_t* wcnt,
+                                             long long (&c)[2], unsigned long long& seen) {
+  if (MODE == mWrite)
+    l2_batch<MODE>(P, A, s, j0, v0, arc0, lane, wcnt, c, seen);
+  else
+    l2_count_batch<MODE>(P, A, s, hA, j0, v0, arc0, lane, wcnt, c, seen);
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(512, 2) motif_l2_warp(MotifArgs P) {
   extern __shared__ int32_t smem[];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   int32_t* A = smem + wid * (P.cap + 32);
@@ -247,7 +350,8 @@ __global__ void __launch_bounds__(512) motif_l2_warp(MotifArgs P) {
         }
       }
       const int64_t arc0 = (int64_t)u0 - P.a_base;
-      for (int j0 = 0; j0 < s; j0 += 32) l2_batch<MODE>(P, A, s, j0, v0, arc0, lane, wcnt, c, seen);
+      const int hA = P.hub_idx[v0];
+      for (int j0 = 0; j0 < s; j0 += 32) l2_any_batch<MODE>(P, A, s, hA, j0, v0, arc0, lane, wcnt, c, seen);
       __syncwarp();
     }
   }
@@ -257,7 +361,7 @@ __global__ void __launch_bounds__(512) motif_l2_warp(MotifArgs P) {
 }
 
 template <int MODE>
-__global__ void __launch_bounds__(512) motif_l2_block(MotifArgs P) {
+__global__ void __launch_bounds__(512, 2) motif_l2_block(MotifArgs P) {
   extern __shared__ int32_t smem[];
   __shared__ long long sh_idx;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -292,8 +396,9 @@ __global__ void __launch_bounds__(512) motif_l2_block(MotifArgs P) {
       }
     }
     const int64_t arc0 = (int64_t)u0 - P.a_base;
+    const int hA = P.hub_idx[v0];
     for (int j0 = wid * 32; j0 < s; j0 += nw * 32)
-      l2_batch<MODE>(P, A, s, j0, v0, arc0, lane, wcnt, c, seen);
+      l2_any_batch<MODE>(P, A, s, hA, j0, v0, arc0, lane, wcnt, c, seen);
     __syncthreads();
   }
   if (MODE == mSum) flush_patterns<2>(P, c, cur_g, lane);
@@ -302,14 +407,6 @@ __global__ void __launch_bounds__(512) motif_l2_block(MotifArgs P) {
 }
 
 // ------------------------------------------------------------- level 3 (last)
-// Membership of w in a sorted list, or by one bit of a hub's adjacency
-// bitmap when the list's owner is a hub (hb >= 0).  Callers only ask about
-// w above the list's lower threshold, so the bitmap of the full adjacency
-// list answers for the thresholded list too.
-__device__ __forceinline__ bool member(const int32_t* L, int len, int hb, const MotifArgs& P, int32_t w) {
-  if (hb >= 0) return (P.hub_bits[(int64_t)hb * P.hub_words + (w >> 5)] >> (w & 31)) & 1u;
-  return len > 0 && w >= L[0] && w <= L[len - 1] && contains_dev(L, len, w);
-}
 
 // Contribution of one candidate w (adjacency bits a, b, c to v0, v1, v2) of
 // the 3-embedding with memo (a02, a12), given that w is adjacent to v2:
@@ -683,6 +780,9 @@ struct MotifRun {
     P.big_cap = (int64_t)ws.big.cap * 2;
     P.cap = cap;
     P.block_cap = block_cap;
+    P.hub_idx = g.hub_idx;
+    P.hub_bits = g.hub_bits;
+    P.hub_words = g.hub_words;
     return P;
   }
 
