@@ -73,7 +73,7 @@ typedef struct {
   int32_t warp_stage_cap;  /* per-warp shared-memory staging capacity, ints (default 512)     */
   int32_t hub_threshold;   /* segment length that moves a parent to the block-per-parent kernel (default = warp_stage_cap) */
   int32_t blocks_per_sm;   /* persistent-grid blocks per SM (default 0 = occupancy-derived)   */
-  int64_t level_budget;    /* max entries of one materialised level chunk (edge blocking, default 1<<29) */
+  int64_t level_budget;    /* max entries of one materialised level chunk (edge blocking, default 1<<31) */
   int32_t profile;         /* 1 = record per-launch CUDA-event times (pgm_last_profile)       */
   int32_t reverse_ratio;   /* intersect in reverse (scan the shorter list, search the longer)
                               when the longer is this many times longer (default 2)          */

@@ -408,6 +408,33 @@ __global__ void __launch_bounds__(512, 2) motif_l2_block(MotifArgs P) {
 
 // ------------------------------------------------------------- level 3 (last)
 
+// Membership of w in both lists at once: hub bitmaps where the owner has
+// one, otherwise the two binary searches advance in the same loop (their
+// loads are independent, so they overlap).
+__device__ __forceinline__ void member2(const int32_t* A, int s, int hA, const int32_t* B, int nb, int hB,
+                                        const MotifArgs& P, int32_t w, bool& ia, bool& ib) {
+  int ba = 0, na = s, bb = 0, nbb = nb;
+  if (hA >= 0) na = 0;
+  if (hB >= 0) nbb = 0;
+  while (na > 1 || nbb > 1) {
+    if (na > 1) {
+      const int h = na >> 1;
+      ba = A[ba + h] < w ? ba + h : ba;
+      na -= h;
+    }
+    if (nbb > 1) {
+      const int h = nbb >> 1;
+      bb = B[bb + h] < w ? bb + h : bb;
+      nbb -= h;
+    }
+  }
+  // the lower bound of w is ba or ba + 1 (and bb or bb + 1)
+  ia = hA >= 0 ? ((P.hub_bits[(int64_t)hA * P.hub_words + (w >> 5)] >> (w & 31)) & 1u) != 0
+               : (s > 0 && (A[ba] == w || (ba + 1 < s && A[ba + 1] == w)));
+  ib = hB >= 0 ? ((P.hub_bits[(int64_t)hB * P.hub_words + (w >> 5)] >> (w & 31)) & 1u) != 0
+               : (nb > 0 && (B[bb] == w || (bb + 1 < nb && B[bb + 1] == w)));
+}
+
 // Contribution of one candidate w (adjacency bits a, b, c to v0, v1, v2) of
 // the 3-embedding with memo (a02, a12), given that w is adjacent to v2:
 // the canonical test accepts it (region thresholds of the header comment)
@@ -609,8 +636,8 @@ __global__ void __launch_bounds__(kML3Threads, 3) motif_l3_edge(MotifArgs P) {
           const int32_t v2q = __shfl_sync(kFull, v2, q);
           bool hit = false, r1 = false, r2 = false, r3 = false;
           if (ok) {
-            const bool ia = member(A, s, hA, P, w);
-            const bool ib = member(B, nb, hB, P, w);
+            bool ia, ib;
+            member2(A, s, hA, B, nb, hB, P, w, ia, ib);
             const bool gt = w > v2q;
             hit = ia || ib;
             r1 = ia && !ib && gt;
