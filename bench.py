@@ -175,6 +175,8 @@ def main(argv=None):
     ap.add_argument("--edges", type=int, default=28_000_000, help="R-MAT undirected edges")
     ap.add_argument("--k", type=int, default=4, choices=[3, 4, 5],
                     help="clique size of the step (profiling runs; the benchmark is k = 4)")
+    ap.add_argument("--clique-engine", type=int, default=0, choices=[0, 1, 2],
+                    help="profiling: 0 auto, 1 level lists, 2 bitset levels")
     ap.add_argument("--motif-only", type=int, default=0, metavar="N",
                     help="profiling: time only 4-motif counting on a Chung-Lu graph of N vertices")
     args = ap.parse_args(argv)
@@ -211,15 +213,15 @@ def main(argv=None):
     workload = WORKLOAD if full else WORKLOAD.replace("scale 21", f"scale {args.scale}").replace(
         "28,000,000", f"{args.edges:,}")
     k = args.k
-    if k != 4:
+    if k != 4 or args.clique_engine:
         workload = workload.replace("4-clique", f"{k}-clique")
-        full = False  # the benchmark line is the 4-clique count
+        full = False  # the benchmark line is the 4-clique count with the default engine
     lo, hi = vertex_shares(g, world)[rank]
     stream = torch.cuda.Stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     G = pgm.Graph(g, stream=stream)
     G.orient()
-    pgm.pgm_set_options(profile=1)
+    pgm.pgm_set_options(profile=1, clique_engine=args.clique_engine)
 
     def step():
         return pgm.pgm_count_kcliques_range(G.h, k, lo, hi)

@@ -106,18 +106,53 @@ __device__ __forceinline__ void bm_filter_size(int d, int cap, int& fw, int& fsh
   fshift = 32 - (__ffs(fw) - 1) - 5;  // 32 * fw bits
 }
 
+// Position of x in P by binary search, or -1.
+struct BmSearch {
+  const int32_t* P;
+  int d;
+  __device__ __forceinline__ int operator()(int32_t x) const {
+    const int j = bm_lower_bound(P, d, x);
+    return (j < d && P[j] == x) ? j : -1;
+  }
+};
+
+// Position of x in P by an open-addressing table (linear probing, at most
+// half full): keys K (-1 = empty) and positions Pos, T = mask + 1 slots.
+__device__ __forceinline__ uint32_t bm_thash(int32_t x, int shift) {
+  return ((uint32_t)x * 0x85EBCA6Bu) >> shift;
+}
+
+struct BmTable {
+  const int32_t* K;
+  const uint16_t* Pos;
+  uint32_t mask;
+  int shift;
+  __device__ __forceinline__ int operator()(int32_t x) const {
+    uint32_t h = bm_thash(x, shift);
+    for (uint32_t probe = 0; probe <= mask; probe++) {
+      const int32_t k = K[h];
+      if (k == x) return Pos[h];
+      if (k < 0) return -1;
+      h = (h + 1) & mask;
+    }
+    return -1;
+  }
+};
+
 // Sets bit j of `row` when P[j] == x.
-__device__ __forceinline__ void bm_locate(const int32_t* P, int d, int32_t x, uint32_t* row) {
-  const int j = bm_lower_bound(P, d, x);
-  if (j < d && P[j] == x) atomicOr(row + (j >> 5), 1u << (j & 31));
+template <class Loc>
+__device__ __forceinline__ void bm_locate(const Loc& loc, int32_t x, uint32_t* row) {
+  const int j = loc(x);
+  if (j >= 0) atomicOr(row + (j >> 5), 1u << (j & 31));
 }
 
 // Forward build of one row by one warp: scan N+(v) (col[b0, b0 + dv)),
 // reject elements with the filter, queue the survivors in q (64 entries)
 // and locate them 32 at a time, so that the binary searches run on full
 // warps.  The row must be zero beforehand.
+template <class Loc>
 __device__ __forceinline__ void bm_row_forward(const int32_t* __restrict__ col, int32_t b0, int32_t dv,
-                                               const int32_t* P, int d, const uint32_t* F, int fshift,
+                                               const Loc& loc, const uint32_t* F, int fshift,
                                                int32_t* q, uint32_t* row, int lane) {
   constexpr int U = 4;  // loads in flight per lane
   const unsigned lt = (1u << lane) - 1u;
@@ -137,7 +172,7 @@ __device__ __forceinline__ void bm_row_forward(const int32_t* __restrict__ col, 
       cnt += __popc(bal);
       if (cnt >= 32) {
         __syncwarp();
-        bm_locate(P, d, q[lane], row);
+        bm_locate(loc, q[lane], row);
         __syncwarp();
         if (lane < cnt - 32) q[lane] = q[lane + 32];
         cnt -= 32;
@@ -146,7 +181,7 @@ __device__ __forceinline__ void bm_row_forward(const int32_t* __restrict__ col, 
     }
   }
   __syncwarp();
-  if (lane < cnt) bm_locate(P, d, q[lane], row);
+  if (lane < cnt) bm_locate(loc, q[lane], row);
   __syncwarp();
 }
 
@@ -228,7 +263,7 @@ __global__ void __launch_bounds__(256, 6) bm_warp_kernel(BmArgs B) {
         const int32_t b0 = sB0[wid][i], dv = sDv[wid][i];
         if (lane == 0) seen += (unsigned long long)dv;
         if ((int64_t)dv <= (int64_t)B.fwd_ratio * d)
-          bm_row_forward(B.col, b0, dv, P, d, F, kWarpFShift, sQ[wid], R + 2 * i, lane);
+          bm_row_forward(B.col, b0, dv, BmSearch{P, d}, F, kWarpFShift, sQ[wid], R + 2 * i, lane);
         else
           bm_row_reverse(B.col, b0, dv, P, d, R + 2 * i, lane);
       }
@@ -343,6 +378,7 @@ __host__ __device__ constexpr size_t bm_block_smem(int dmax, int threads) {
   return dmax > 0 ? (size_t)4 * dmax                       // P
                         + (size_t)8 * dmax                  // start and length of each out-list
                         + (size_t)4 * dmax                  // filter (up to dmax words)
+                        + (size_t)(4 + 2) * 2 * dmax        // position table: 2 dmax keys + positions
                         + (size_t)4 * (threads / 32) * 128  // two 64-entry buffers per warp
                         + (size_t)16 * (threads / 32) * bm_s4(dmax / 32)  // C = R_i & R_j per warp
                         + (size_t)16 * dmax * bm_s4(dmax / 32)            // rows
@@ -362,13 +398,15 @@ __global__ void __launch_bounds__(THREADS, bm_min_blocks(DMAX, THREADS)) bm_bloc
   extern __shared__ __align__(16) uint32_t smem_u[];
   __shared__ long long sh_idx;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  // layout (DMAX > 0): P | B0 | Dv | filter | buffers | C | rows;
+  // layout (DMAX > 0): P | B0 | Dv | filter | table keys | table positions | buffers | C | rows;
   // (DMAX = 0): filter | buffers
-  constexpr int kHead = DMAX > 0 ? 4 * DMAX : kBmGlobalFW;
+  constexpr int kHead = DMAX > 0 ? 7 * DMAX : kBmGlobalFW;
   int32_t* sP = reinterpret_cast<int32_t*>(smem_u);
   int32_t* sB0 = sP + DMAX;
   int32_t* sDv = sB0 + DMAX;
   uint32_t* sF = smem_u + (DMAX > 0 ? 3 * DMAX : 0);
+  int32_t* sK = reinterpret_cast<int32_t*>(smem_u) + 4 * DMAX;
+  uint16_t* sPos = reinterpret_cast<uint16_t*>(smem_u + 6 * DMAX);
   int* buf = reinterpret_cast<int*>(smem_u) + kHead + wid * 128;
   int* buf2 = buf + 64;
   uint32_t* sC = smem_u + kHead + NW * 128 + wid * 4 * S4MAX;
@@ -417,10 +455,30 @@ __global__ void __launch_bounds__(THREADS, bm_min_blocks(DMAX, THREADS)) bm_bloc
       R = gRows;
     }
     for (int i = threadIdx.x; i < fw; i += THREADS) sF[i] = 0;
+    uint32_t tmask = 0;
+    int tshift = 0;
+    if constexpr (DMAX > 0) {
+      int T = 64;
+      while (T < 2 * d) T <<= 1;
+      tmask = (uint32_t)T - 1u;
+      tshift = 32 - (__ffs(T) - 1);
+      for (int i = threadIdx.x; i < T; i += THREADS) sK[i] = -1;
+    }
     __syncthreads();
     for (int i = threadIdx.x; i < d; i += THREADS) {
-      const uint32_t h = bm_fhash(P[i], fshift);
+      const int32_t x = P[i];
+      const uint32_t h = bm_fhash(x, fshift);
       atomicOr(sF + (h >> 5), 1u << (h & 31));
+      if constexpr (DMAX > 0) {
+        uint32_t t = bm_thash(x, tshift);
+        for (uint32_t probe = 0; probe <= tmask; probe++) {
+          if (atomicCAS(sK + t, -1, x) == -1) {
+            sPos[t] = (uint16_t)i;
+            break;
+          }
+          t = (t + 1) & tmask;
+        }
+      }
     }
     __syncthreads();
     // rows R_i = N+(P[i]) & P, one warp per row
@@ -437,7 +495,10 @@ __global__ void __launch_bounds__(THREADS, bm_min_blocks(DMAX, THREADS)) bm_bloc
       uint32_t* row = R + (int64_t)i * S;
       if (lane == 0) seen += (unsigned long long)dv;
       if ((int64_t)dv <= (int64_t)B.fwd_ratio * d)
-        bm_row_forward(B.col, b0, dv, P, d, sF, fshift, buf, row, lane);
+        if constexpr (DMAX > 0)
+          bm_row_forward(B.col, b0, dv, BmTable{sK, sPos, tmask, tshift}, sF, fshift, buf, row, lane);
+        else
+          bm_row_forward(B.col, b0, dv, BmSearch{P, d}, sF, fshift, buf, row, lane);
       else
         bm_row_reverse(B.col, b0, dv, P, d, row, lane);
     }
