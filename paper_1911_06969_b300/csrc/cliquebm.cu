@@ -166,7 +166,7 @@ __device__ __forceinline__ void bm_row_forward(const int32_t* __restrict__ col, 
     }
 #pragma unroll
     for (int r = 0; r < U; r++) {
-      const bool cand = x[r] >= 0 && bm_fhit(F, fshift, x[r]);
+      const bool cand = (x[r] >= 0) & bm_fhit(F, fshift, x[r]);
       const unsigned bal = __ballot_sync(kFull, cand);
       if (cand) q[cnt + __popc(bal & lt)] = x[r];
       cnt += __popc(bal);
