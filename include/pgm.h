@@ -81,7 +81,7 @@ typedef struct {
                               1 = level lists (vid arrays + inspection-execution),
                               2 = bitset levels where supported                               */
   int32_t bitset_forward_ratio;  /* bitset rows: build row i by scanning N+(P[i]) when it is at most
-                                    this many times longer than P, else by testing P in it (default 8) */
+                                    this many times longer than P, else by testing P in it (default 4) */
   int32_t bitset_smem_degree;    /* bitset rows: largest out-degree whose rows live in shared memory;
                                     64, 256, 512 or 1024 (default 1024); larger ones use global scratch */
   int32_t reserved[3];

@@ -187,11 +187,29 @@ __device__ __forceinline__ void bm_row_forward(const int32_t* __restrict__ col, 
 
 // Reverse build of one row by one warp: test each P[j] against N+(v) by
 // binary search in global memory; one ballot word per 32 positions.
+// N+(v) is cut into 32 segments of S elements; lane l holds the last
+// element of segment l, so a search first picks the segment among the lanes
+// (shuffles) and then searches S elements in memory.
 __device__ __forceinline__ void bm_row_reverse(const int32_t* __restrict__ col, int32_t b0, int32_t dv,
                                                const int32_t* P, int d, uint32_t* row, int lane) {
+  const int S = (dv + 31) >> 5;
+  const int s0 = lane * S;
+  const int32_t key = s0 < dv ? col[b0 + min(s0 + S, dv) - 1] : INT32_MAX;
   for (int j0 = 0; j0 < d; j0 += 32) {
     const int j = j0 + lane;
-    const bool in = j < d && contains_dev(col + b0, dv, P[j]);
+    const int32_t x = j < d ? P[j] : INT32_MAX;
+    int seg = 0;  // first segment whose last element is >= x
+#pragma unroll
+    for (int step = 16; step > 0; step >>= 1) {
+      const int32_t k = __shfl_sync(kFull, key, seg + step - 1);
+      if (k < x) seg += step;
+    }
+    const int32_t kseg = __shfl_sync(kFull, key, seg);
+    bool in = false;
+    if (j < d && kseg >= x) {
+      const int lo = seg * S;
+      in = contains_dev(col + b0 + lo, min(lo + S, dv) - lo, x);
+    }
     const unsigned bal = __ballot_sync(kFull, in);
     if (lane == 0 && bal) row[j0 >> 5] |= bal;
   }

@@ -122,7 +122,7 @@ def test_bitset_buckets(smem_degree, fwd):
         assert gpu_cliques(gg.complete_multipartite(sizes), [3, 4]) == want
         assert gpu_cliques(gg.complete(1100), [3, 4]) == [math.comb(1100, k) for k in (3, 4)]
     finally:
-        pgm.pgm_set_options(clique_engine=0, bitset_smem_degree=1024, bitset_forward_ratio=8)
+        pgm.pgm_set_options(clique_engine=0, bitset_smem_degree=1024, bitset_forward_ratio=4)
 
 
 def test_small_tiles_hub_paths(small_tiles):
