@@ -682,11 +682,8 @@ __global__ void __launch_bounds__(kML3Threads, 3) motif_l3_edge(MotifArgs P) {
 #pragma unroll
           for (int r = 0; r < kU; r++) {
             const int32_t w = wv[r];
-            bool cand = false;
-            if (w >= 0 && w != v1) {
-              const uint32_t h = mf_hash(w, fshift);
-              cand = (F[h >> 5] >> (h & 31)) & 1u;
-            }
+            const uint32_t h = mf_hash(w, fshift);  // branch-free: w = -1 hashes in range too
+            const bool cand = (w >= 0) & (w != v1) & (((F[h >> 5] >> (h & 31)) & 1u) != 0);
             const unsigned bal = __ballot_sync(kFull, cand);
             if (cand) {
               const int pos = qn + __popc(bal & lt);
