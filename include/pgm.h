@@ -66,8 +66,8 @@ typedef struct {
 } pgm_graph_stats;
 
 /* Tunables (pgm_set_options / pgm_get_options).  A zero field keeps the
- * current value, except `profile` and `clique_engine`, which every call
- * sets (0 = off / auto). */
+ * current value, except `profile`, `clique_engine` and `motif_order`, which
+ * every call sets (0 = off / auto). */
 typedef struct {
   int32_t block_threads;   /* threads per block of the warp-per-parent kernels, 64..512 (default 256) */
   int32_t warp_stage_cap;  /* per-warp shared-memory staging capacity, ints (default 512)     */
@@ -84,7 +84,10 @@ typedef struct {
                                     this many times longer than P, else by testing P in it (default 4) */
   int32_t bitset_smem_degree;    /* bitset rows: largest out-degree whose rows live in shared memory;
                                     64, 256, 512 or 1024 (default 1024); larger ones use global scratch */
-  int32_t reserved[3];
+  int32_t motif_order;           /* full-range motif counts: 0 = on a copy relabelled by degree
+                                    (ascending for k = 3, descending for k = 4; counts are unchanged),
+                                    1 = on the input IDs (every call sets this field)              */
+  int32_t reserved[2];
 } pgm_options;
 
 /* Per-call profile (when options.profile = 1): one record per kernel phase. */

@@ -29,7 +29,7 @@ const char* get_error() { return t_err.c_str(); }
 static std::atomic<uint64_t> g_launches{0};
 void note_launches(uint64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
-static pgm_options g_opts = {256, 512, 0, 0, (int64_t)1 << 31, 0, 2, 0, 4, 1024, {0}};
+static pgm_options g_opts = {256, 512, 0, 0, (int64_t)1 << 31, 0, 2, 0, 4, 1024, 0, {0}};
 
 pgm_options& options() { return g_opts; }
 
@@ -291,6 +291,11 @@ pgm_status pgm_set_options(const pgm_options* o) {
     }
     next.bitset_smem_degree = b;
   }
+  if (v.motif_order < 0 || v.motif_order > 1) {
+    pgm::set_error("motif_order must be 0 (degree-ordered copy) or 1 (input IDs)");
+    return PGM_EINVAL;
+  }
+  next.motif_order = v.motif_order;
   next.profile = v.profile ? 1 : 0;
   pgm::options() = next;
   return PGM_OK;

@@ -10,6 +10,7 @@
 #include <cstdint>
 #include <cstdio>
 #include <string>
+#include <memory>
 #include <mutex>
 #include <vector>
 
@@ -130,6 +131,7 @@ struct Graph {
   int32_t* up = nullptr;       // up[v] = first arc of v whose neighbour is > v
   int32_t* gid = nullptr;      // batches: vertex -> graph id (nullptr otherwise)
   int32_t* src = nullptr;      // motifs: source vertex of every arc
+  int32_t* rev = nullptr;      // motifs: index of the reverse arc (v -> u) of every arc u -> v
   int32_t* hub_idx = nullptr;  // motifs: vertex -> row of hub_bits, or -1
   uint32_t* hub_bits = nullptr;  // motifs: adjacency bitmaps of the highest-degree vertices
   int64_t hub_words = 0;       // 32-bit words per bitmap row
@@ -140,9 +142,12 @@ struct Graph {
   cudaStream_t stream = nullptr;
   std::vector<int64_t> h_dag_rp;  // host copy of the DAG row pointers (edge blocking), lazy
   std::vector<int64_t> h_rp;      // host copy of the CSR row pointers, lazy
-  std::recursive_mutex mu;        // orientation and the lazy host copies
+  std::recursive_mutex mu;        // orientation, lazy host copies, motif helpers, relabelled copies
   Workspace ws;                   // workspace of calls made through the handle
+  std::unique_ptr<Graph> relabeled[2];  // copies with IDs in ascending / descending degree order
 };
+
+constexpr int kOrderAscending = 0, kOrderDescending = 1;
 
 pgm_status graph_upload(Graph& g, int32_t n, const int64_t* rowptr, const int32_t* col,
                         bool rowptr_on_device, int64_t narcs, uint32_t flags, cudaStream_t s);
@@ -154,6 +159,11 @@ pgm_status graph_host_rp(Graph& g);
 pgm_status graph_host_dag_rp(Graph& g);
 // arcs of the DAG whose source lies in [v_lo, v_hi)
 pgm_status graph_dag_arcs(Graph& g, int32_t v_lo, int32_t v_hi, int64_t* arcs);
+// copy of g with vertex IDs in degree order (kOrderAscending / kOrderDescending),
+// each graph of a batch within its own block; built on first use
+pgm_status graph_relabeled(Graph& g, int order, Graph** out);
+// out[i] = (int32) in[i] on the stream
+void narrow_rowptr(const int64_t* in, int32_t* out, int64_t len, cudaStream_t s);
 void graph_free(Graph& g);
 
 // scan: out[i] = sum cnt[0..i), out[len] = total (device pointers)

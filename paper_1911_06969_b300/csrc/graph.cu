@@ -148,6 +148,19 @@ __global__ void src_kernel(int32_t n, const int32_t* __restrict__ rp, int32_t* _
     for (int32_t a = rp[v] + lane; a < rp[v + 1]; a += 32) src[a] = (int32_t)v;
 }
 
+// rev[a] = index of arc v -> u for every arc a = u -> v (binary search in N(v))
+__global__ void rev_kernel(int32_t n, const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
+                           int32_t* __restrict__ rev) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t u = warp; u < n; u += nwarps)
+    for (int32_t a = rp[u] + lane; a < rp[u + 1]; a += 32) {
+      const int32_t v = col[a];
+      rev[a] = rp[v] + lower_bound_dev(col + rp[v], rp[v + 1] - rp[v], (int32_t)u);
+    }
+}
+
 // one block per hub: set the bits of its neighbours in its bitmap row
 __global__ void hub_bits_kernel(const int32_t* __restrict__ hubs, int32_t nh, const int32_t* __restrict__ rp,
                                 const int32_t* __restrict__ col, uint32_t* __restrict__ bits, int64_t words) {
@@ -191,7 +204,17 @@ static void sanitize_host(int32_t n, const int64_t* rowptr, const int32_t* col,
   for (int32_t v = 0; v < n; v++) rp_out[v + 1] += rp_out[v];
 }
 
+void narrow_rowptr(const int64_t* in, int32_t* out, int64_t len, cudaStream_t s) {
+  narrow_kernel<<<std::max(1, std::min(num_sms() * 8, (int)((len + 255) / 256))), 256, 0, s>>>(in, out, len);
+  note_launches(1);
+}
+
 void graph_free(Graph& g) {
+  for (auto& r : g.relabeled)
+    if (r) {
+      graph_free(*r);
+      r.reset();
+    }
   if (g.rp) cudaFree(g.rp);
   if (g.col) cudaFree(g.col);
   if (g.dag_rp) cudaFree(g.dag_rp);
@@ -199,9 +222,10 @@ void graph_free(Graph& g) {
   if (g.gid) cudaFree(g.gid);
   if (g.up) cudaFree(g.up);
   if (g.src) cudaFree(g.src);
+  if (g.rev) cudaFree(g.rev);
   if (g.hub_idx) cudaFree(g.hub_idx);
   if (g.hub_bits) cudaFree(g.hub_bits);
-  g.rp = g.col = g.dag_rp = g.dag_col = g.gid = g.up = g.src = g.hub_idx = nullptr;
+  g.rp = g.col = g.dag_rp = g.dag_col = g.gid = g.up = g.src = g.hub_idx = g.rev = nullptr;
   g.hub_bits = nullptr;
   g.nhubs = 0;
   g.ws.release_all();
@@ -400,12 +424,14 @@ constexpr int64_t kHubDegree = 512;  // longer lists than the default staging ca
 constexpr int64_t kHubBytes = (int64_t)512 << 20;
 
 pgm_status graph_prepare_motifs(Graph& g) {
+  std::lock_guard<std::recursive_mutex> lk(g.mu);
   if (g.up) return PGM_OK;
   PGM_TRY(graph_host_rp(g));
   cudaStream_t s = g.stream;
   const int32_t n = g.n;
   PGM_TRY_CUDA(cudaMalloc(&g.up, ((size_t)n + 1) * sizeof(int32_t)));
   PGM_TRY_CUDA(cudaMalloc(&g.src, (size_t)std::max<int64_t>(g.narcs, 1) * sizeof(int32_t)));
+  PGM_TRY_CUDA(cudaMalloc(&g.rev, (size_t)std::max<int64_t>(g.narcs, 1) * sizeof(int32_t)));
   PGM_TRY_CUDA(cudaMalloc(&g.hub_idx, ((size_t)n + 1) * sizeof(int32_t)));
   PGM_TRY_CUDA(cudaMemsetAsync(g.hub_idx, 0xff, ((size_t)n + 1) * sizeof(int32_t), s));
   if (n > 0) {
@@ -413,6 +439,8 @@ pgm_status graph_prepare_motifs(Graph& g) {
     upper_kernel<<<blocks, 256, 0, s>>>(n, g.rp, g.col, g.up);
     PGM_CHECK_LAUNCH();
     src_kernel<<<warp_grid(n, 256), 256, 0, s>>>(n, g.rp, g.src);
+    PGM_CHECK_LAUNCH();
+    rev_kernel<<<warp_grid(n, 256), 256, 0, s>>>(n, g.rp, g.col, g.rev);
     PGM_CHECK_LAUNCH();
   }
   // hubs: highest degrees first

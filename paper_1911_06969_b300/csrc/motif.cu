@@ -95,6 +95,8 @@ struct MotifArgs {
   const uint32_t* hub_bits; // adjacency bitmaps of hub vertices
   int64_t hub_words;        // words per bitmap row
   int rev_ratio;            // reverse scan when d(v2) > rev_ratio * (|A| + |B|)
+  uint32_t* hubctr;         // level 2, counting modes: next 32-entry batch of each hub vertex
+  const int32_t* rev;       // rev[a] = index of the reverse arc of arc a
 };
 
 template <int N>
@@ -232,7 +234,8 @@ __device__ __forceinline__ void l2_count_batch(const MotifArgs& P, const int32_t
     v1 = A[j];
     r1 = P.rp[v1];
     d1 = P.rp[v1 + 1] - r1;
-    const int bs = lower_bound_dev(P.col + r1, d1, v0 + 1);
+    // N(v1) & (v0, inf) starts after v0's own entry in N(v1) (the reverse arc)
+    const int bs = P.rev[P.a_base + arc0 + j] - r1 + 1;
     b0 = r1 + bs;
     nbj = d1 - bs;
     hv1 = P.hub_idx[v1];
@@ -354,6 +357,54 @@ __global__ void __launch_bounds__(512, 2) motif_l2_warp(MotifArgs P) {
       for (int j0 = 0; j0 < s; j0 += 32) l2_any_batch<MODE>(P, A, s, hA, j0, v0, arc0, lane, wcnt, c, seen);
       __syncwarp();
     }
+  }
+  if (MODE == mSum) flush_patterns<2>(P, c, cur_g, lane);
+  seen = warp_sum(seen);
+  if (lane == 0 && seen) atomicAdd(P.stat, seen);
+}
+
+// Counting modes: the segments of the hub vertices (deferred by the warp
+// kernel) in batches of 32 entries, taken by any warp from a per-hub
+// counter, with A read in place (hub bitmap for membership) -- no block
+// barrier, so a long batch delays no other warp.  Warps move through the
+// hub list in order; `hint` (queue[3]) is the first hub not known to be
+// exhausted.
+template <int MODE>
+__global__ void __launch_bounds__(256) motif_l2_hubs(MotifArgs P) {
+  __shared__ uint32_t wcnt_all[8][32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  uint32_t* wcnt = wcnt_all[wid];
+  long long c[2] = {0, 0};
+  unsigned long long seen = 0;
+  int cur_g = -1;
+  const long long nbig = min((long long)P.queue[2], (long long)P.big_cap);
+  unsigned long long* hint = P.queue + 3;
+  long long i = 0;
+  if (lane == 0) i = (long long)atomicAdd(hint, 0ull);
+  i = __shfl_sync(kFull, i, 0);
+  while (i < nbig) {
+    const int32_t v0 = P.big[i];
+    const int32_t u0 = P.up[v0];
+    const int s = P.rp[v0 + 1] - u0;
+    unsigned b = 0;
+    if (lane == 0) b = atomicAdd(P.hubctr + i, 1u);
+    b = __shfl_sync(kFull, b, 0);
+    if ((long long)b * 32 >= s) {  // hub i exhausted: move on
+      unsigned long long h = 0;
+      if (lane == 0) h = atomicMax(hint, (unsigned long long)(i + 1));
+      h = __shfl_sync(kFull, h, 0);
+      i = max(i + 1, (long long)h);
+      continue;
+    }
+    if (MODE == mSum && P.gid) {
+      const int g = P.gid[v0];
+      if (g != cur_g) {
+        flush_patterns<2>(P, c, cur_g, lane);
+        cur_g = g;
+      }
+    }
+    const int64_t arc0 = (int64_t)u0 - P.a_base;
+    l2_count_batch<MODE>(P, P.col + u0, s, P.hub_idx[v0], (int)b * 32, v0, arc0, lane, wcnt, c, seen);
   }
   if (MODE == mSum) flush_patterns<2>(P, c, cur_g, lane);
   seen = warp_sum(seen);
@@ -536,8 +587,7 @@ __global__ void __launch_bounds__(kML3Threads, 3) motif_l3_edge(MotifArgs P) {
       }
       const int32_t r0 = P.rp[v1], r1 = P.rp[v1 + 1];
       int bstart = 0;
-      if (lane == 0) bstart = lower_bound_dev(P.col + r0, r1 - r0, v0 + 1);
-      bstart = __shfl_sync(kFull, bstart, 0);
+      bstart = P.rev[a] - r0 + 1;  // after v0's own entry in N(v1)
       const int nb = r1 - r0 - bstart;
       const int32_t* B;
       if (nb <= P.cap) {
@@ -807,12 +857,18 @@ struct MotifRun {
     P.hub_idx = g.hub_idx;
     P.hub_bits = g.hub_bits;
     P.hub_words = g.hub_words;
+    P.rev = g.rev;
     return P;
   }
 
   template <int MODE>
   pgm_status launch_l2(MotifArgs P, const char* name) {
     PGM_TRY_CUDA(cudaMemsetAsync(ctr() + kQ, 0, 4 * sizeof(unsigned long long), s));
+    if (MODE != mWrite) {
+      PGM_TRY(ws.cnt[3].reserve((size_t)std::max<int64_t>(P.big_cap, 1)));
+      PGM_TRY_CUDA(cudaMemsetAsync(ws.cnt[3].p, 0, (size_t)std::max<int64_t>(P.big_cap, 1) * sizeof(uint32_t), s));
+      P.hubctr = ws.cnt[3].p;
+    }
     P.stat = ctr() + kStat + MODE;
     const int threads = o.block_threads;
     const size_t wsmem = (size_t)(threads / 32) * (cap + 32) * sizeof(int32_t);
@@ -828,8 +884,14 @@ struct MotifRun {
     int id = prof.begin(name, 2);
     motif_l2_warp<MODE><<<wgrid, threads, wsmem, s>>>(P);
     PGM_CHECK_LAUNCH();
-    motif_l2_block<MODE><<<bgrid, 512, bsmem, s>>>(P);
-    PGM_CHECK_LAUNCH();
+    if (MODE == mWrite) {
+      motif_l2_block<MODE><<<bgrid, 512, bsmem, s>>>(P);
+      PGM_CHECK_LAUNCH();
+    } else {
+      const int hgrid = grid_for((const void*)motif_l2_hubs<MODE>, 256, 0);
+      motif_l2_hubs<MODE><<<hgrid, 256, 0, s>>>(P);
+      PGM_CHECK_LAUNCH();
+    }
     prof.end(id, (double)(g.h_rp[P.v_hi] - g.h_rp[P.v_lo]) / 2.0, 0.0);
     return PGM_OK;
   }
@@ -938,6 +1000,9 @@ struct MotifRun {
 
 }  // namespace
 
+pgm_status count_motifs_on(Graph& g, Workspace& ws, cudaStream_t s, int k, int32_t v_lo, int32_t v_hi,
+                           uint64_t* out, unsigned long long* per_graph_dev);
+
 pgm_status count_motifs(Graph& g, Workspace& ws, cudaStream_t s, int k, int32_t v_lo, int32_t v_hi,
                         uint64_t* out, unsigned long long* per_graph_dev) {
   if (k != 3 && k != 4) {
@@ -952,6 +1017,17 @@ pgm_status count_motifs(Graph& g, Workspace& ws, cudaStream_t s, int k, int32_t 
     set_error("count_motifs: n=%d needs 30-bit vertex IDs", g.n);
     return PGM_EUNSUPPORTED;
   }
+  if (v_lo == 0 && v_hi == g.n && g.n > 0 && options().motif_order == 0) {
+    // full range: count on the copy relabelled by degree (same counts, less work)
+    Graph* r = nullptr;
+    PGM_TRY(graph_relabeled(g, k == 3 ? kOrderAscending : kOrderDescending, &r));
+    return count_motifs_on(*r, ws, s, k, 0, r->n, out, per_graph_dev);
+  }
+  return count_motifs_on(g, ws, s, k, v_lo, v_hi, out, per_graph_dev);
+}
+
+pgm_status count_motifs_on(Graph& g, Workspace& ws, cudaStream_t s, int k, int32_t v_lo, int32_t v_hi,
+                           uint64_t* out, unsigned long long* per_graph_dev) {
   MotifRun run(g, ws, s, k);
   run.per_graph = per_graph_dev;
   PGM_TRY(run.prepare());

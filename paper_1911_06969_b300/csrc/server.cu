@@ -189,6 +189,12 @@ pgm_status pgm_server_add_graph(pgm_server* s, int32_t n, const int64_t* rowptr,
   if (st == PGM_OK) st = pgm::graph_orient(sg->g);
   if (st == PGM_OK) st = pgm::graph_prepare_motifs(sg->g);
   if (st == PGM_OK) st = pgm::graph_host_dag_rp(sg->g);  // before any worker uses the graph
+  // the relabelled copies the motif queries count on, prepared before any worker uses them
+  for (int order = 0; order < 2 && st == PGM_OK; order++) {
+    pgm::Graph* r = nullptr;
+    st = pgm::graph_relabeled(sg->g, order, &r);
+    if (st == PGM_OK) st = pgm::graph_prepare_motifs(*r);
+  }
   if (st != PGM_OK) {
     pgm::graph_free(sg->g);
     return st;

@@ -57,7 +57,7 @@ class pgm_options(C.Structure):
                 ("blocks_per_sm", C.c_int32), ("level_budget", C.c_int64), ("profile", C.c_int32),
                 ("reverse_ratio", C.c_int32), ("clique_engine", C.c_int32),
                 ("bitset_forward_ratio", C.c_int32), ("bitset_smem_degree", C.c_int32),
-                ("reserved", C.c_int32 * 3)]
+                ("motif_order", C.c_int32), ("reserved", C.c_int32 * 2)]
 
 
 class pgm_phase(C.Structure):

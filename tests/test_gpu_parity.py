@@ -125,6 +125,20 @@ def test_bitset_buckets(smem_degree, fwd):
         pgm.pgm_set_options(clique_engine=0, bitset_smem_degree=1024, bitset_forward_ratio=4)
 
 
+@pytest.mark.parametrize("order", [0, 1])
+def test_motif_orders(order):
+    """Motif counts on the degree-relabelled copy (order 0) and on the input IDs
+    (order 1) both equal the oracle's, for graphs with hubs of both kinds of ID."""
+    pgm.pgm_set_options(motif_order=order)
+    try:
+        for g in [gg.barabasi_albert(3000, 7, seed=21), gg.rmat(1 << 12, 30000, seed=22),
+                  gg.chung_lu(4096, 2.1, 10.0, 500.0, 23), gg.star(50), gg.complete_multipartite((9, 10, 11))]:
+            for k in (3, 4):
+                assert gpu_motifs(g, k) == oracle.formula_motifs(g, k), (g.name, k, order)
+    finally:
+        pgm.pgm_set_options(motif_order=0)
+
+
 def test_small_tiles_hub_paths(small_tiles):
     for g in [gg.barabasi_albert(2000, 12, seed=8), gg.complete(80), gg.rmat(1 << 12, 30000, seed=9),
               gg.complete_multipartite((30, 30, 30))]:
