@@ -367,7 +367,11 @@ def extras(pgm, torch, stream, flush):
     gold = load_json(os.path.join(GOLD, "chung_lu_1m.json"))
     pgm.pgm_set_options(profile=1)
     with pgm.Graph(g, stream=stream) as G:
-        G.motifs(4)
+        torch.cuda.synchronize()
+        t_first = time.perf_counter()
+        G.motifs(4)  # first call: also builds the degree-relabelled copy and the motif helpers
+        torch.cuda.synchronize()
+        t_first = (time.perf_counter() - t_first) * 1e3
         ms, dom_ms, dom_b = [], 0.0, 0.0
         for _ in range(2):
             with torch.cuda.stream(stream):
@@ -390,6 +394,7 @@ def extras(pgm, torch, stream, flush):
     out["motif4_chung_lu_1m"] = {
         "value": emb / (t * 1e-3), "unit": "embeddings/s", "ms_per_step": t, "counts": m4,
         "exact_vs_oracle": (gold["motif4"] == m4) if gold else None, "embeddings_per_step": emb,
+        "first_call_ms": t_first,
         "last_level_alg_GBps": dom_b / (dom_ms * 1e-3) / 1e9 if dom_ms else None}
     # batched many-small-graphs path vs the per-graph loop
     b = gg.small_batch_20k()

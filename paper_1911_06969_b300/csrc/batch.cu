@@ -387,17 +387,23 @@ pgm_status pgm_batch_count_motifs_loop(pgm_batch* b, int32_t k, uint64_t* out) {
     return PGM_EUNSUPPORTED;
   }
   const int np = k == 3 ? 2 : 6;
-  pgm::Graph& g = b->g;
-  // the per-graph view: the union's arrays restricted to one graph's range
+  // the same graph the batched pass counts on (the relabelled copy keeps
+  // every graph's block of IDs), restricted to one graph's range per call
   // (no per-graph attribution; one plain engine call per graph)
+  pgm::Graph* gp = &b->g;
+  if (pgm::options().motif_order == 0) {
+    pgm_status rs = pgm::graph_relabeled(b->g, k == 3 ? pgm::kOrderAscending : pgm::kOrderDescending, &gp);
+    if (rs != PGM_OK) return rs;
+  }
+  pgm::Graph& g = *gp;
   int32_t* gid = g.gid;
   g.gid = nullptr;
   pgm_status st = PGM_OK;
   for (int32_t i = 0; i < b->G && st == PGM_OK; i++) {
     pgm::profiler().start(g.stream);
     uint64_t c[6];
-    st = pgm::count_motifs(g, g.ws, g.stream, k, (int32_t)b->vtx_off[i], (int32_t)b->vtx_off[i + 1], c,
-                           nullptr);
+    st = pgm::count_motifs_on(g, b->g.ws, g.stream, k, (int32_t)b->vtx_off[i], (int32_t)b->vtx_off[i + 1], c,
+                              nullptr);
     if (st == PGM_OK) memcpy(out + (int64_t)i * np, c, np * sizeof(uint64_t));
   }
   g.gid = gid;
