@@ -162,6 +162,16 @@ pgm_status pgm_count_kcliques(pgm_graph *g, int32_t k, uint64_t *out_count);
 pgm_status pgm_count_kcliques_range(pgm_graph *g, int32_t k, int32_t v_lo, int32_t v_hi,
                                     uint64_t *out_count);
 
+/* List the k-cliques (1 <= k <= 10; Sec. 3.3 Listing 3 with the last level
+ * written instead of reduced, as the embedding lists of Sec. 5.1 allow).
+ * Writes one row of k vertex IDs per clique into the caller's DEVICE buffer
+ * out_dev (int32, cap_rows * k entries, row-major), the vertices of each row
+ * in the orientation order of the DAG (Sec. 4.1); rows appear in no
+ * particular order.  *n_rows receives the number of cliques.  out_dev = NULL
+ * is a size query (returns PGM_OK with *n_rows set).  PGM_EOVERFLOW (with
+ * *n_rows set) if the cliques exceed cap_rows; nothing is written then. */
+pgm_status pgm_list_kcliques(pgm_graph* g, int32_t k, int32_t* out_dev, int64_t cap_rows, int64_t* n_rows);
+
 /* Vertex-induced motif counts (Sec. 2.2; Sec. 3.3 Listing 4 "motif
  * counting"; customised classification Sec. 4.2, Listing 6): for each
  * connected k-vertex pattern, the number of vertex sets whose induced

@@ -45,6 +45,46 @@ struct Lvl {
   int64_t e_lo, e_hi;    // entry range (after shift) of the parents
 };
 
+// Listing: every entry of the last level becomes a row of k vertex IDs.
+// The vertex at position l of the row is vid_l[e_l], and the parent of a
+// level-l entry e_l is the parent p whose segment holds it (the largest p
+// with seg_l[p] - shift_l <= e_l); p indexes level l-1 as p + e_lo_{l-1}.
+// Level 2's parents are the vertices themselves (position 1).
+constexpr int kMaxK = 10;
+struct EmitArgs {
+  int k;
+  const void* seg[kMaxK + 1];
+  int seg32[kMaxK + 1];
+  int64_t shift[kMaxK + 1], p_lo[kMaxK + 1], p_hi[kMaxK + 1], e_lo[kMaxK + 1];
+  const int32_t* vid[kMaxK + 1];
+  int64_t n;           // entries of the last level in this chunk
+  int32_t* out;        // rows of k IDs
+  int64_t out_base;    // first row of this chunk
+};
+
+__global__ void emit_kernel(EmitArgs A) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < A.n; t += (int64_t)gridDim.x * blockDim.x) {
+    int64_t e = t + A.e_lo[A.k];
+    int32_t* row = A.out + (A.out_base + t) * A.k;
+    for (int l = A.k; l >= 2; l--) {
+      row[l - 1] = A.vid[l][e];
+      const int64_t key = e + A.shift[l];
+      int64_t lo = A.p_lo[l], hi = A.p_hi[l];  // seg[lo] <= key < seg[hi]
+      while (hi - lo > 1) {
+        const int64_t mid = lo + ((hi - lo) >> 1);
+        const int64_t v = A.seg32[l] ? (int64_t) reinterpret_cast<const int32_t*>(A.seg[l])[mid]
+                                     : reinterpret_cast<const int64_t*>(A.seg[l])[mid];
+        if (v <= key)
+          lo = mid;
+        else
+          hi = mid;
+      }
+      e = lo + A.e_lo[l - 1];
+    }
+    row[0] = (int32_t)e;  // level 1: the vertex itself
+  }
+}
+
 // counter slots in ws.ctr
 constexpr int kSlotQueue = 0;  // 4 per launch (reset per launch)
 constexpr int kSlotErr = 15;   // hub-list overflow counter
@@ -62,6 +102,10 @@ struct CliqueRun {
   int chunks = 0;
   unsigned long long* per_graph = nullptr;
   double lvl_entries[Workspace::kMaxLevels] = {0};
+  // listing mode (list_out != nullptr): the last level is written and emitted
+  int32_t* list_out = nullptr;
+  int64_t list_n = 0;
+  Lvl chain[Workspace::kMaxLevels + 1];
   double lvl_parents[Workspace::kMaxLevels] = {0};
   double lvl_size[Workspace::kMaxLevels + 4] = {0};
 
@@ -162,14 +206,44 @@ struct CliqueRun {
     return PGM_OK;
   }
 
+  // rows for the last level `last` (entries 0..n) of this chunk
+  pgm_status emit(const Lvl& last, int64_t n) {
+    EmitArgs A;
+    memset(&A, 0, sizeof(A));
+    A.k = k;
+    for (int l = 2; l <= k; l++) {
+      const Lvl& L = l == k ? last : chain[l];
+      A.seg[l] = L.seg;
+      A.seg32[l] = L.seg32 ? 1 : 0;
+      A.shift[l] = L.seg_shift;
+      A.p_lo[l] = L.p_lo;
+      A.p_hi[l] = L.p_hi;
+      A.e_lo[l] = L.e_lo;
+      A.vid[l] = L.vid;
+    }
+    A.e_lo[1] = 0;
+    A.n = n;
+    A.out = list_out;
+    A.out_base = list_n;
+    Profiler& prof = profiler();
+    int id = prof.begin("extend_list", k);
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)num_sms() * 8, (n + 255) / 256));
+    emit_kernel<<<blocks, 256, 0, s>>>(A);
+    PGM_CHECK_LAUNCH();
+    prof.end(id, (double)n, 4.0 * (double)k * (double)n);
+    list_n += n;
+    return PGM_OK;
+  }
+
   pgm_status level(int l, const Lvl& L) {
+    chain[l] = L;
     const int64_t E = L.e_hi - L.e_lo;
     const int64_t P = L.p_hi - L.p_lo;
     lvl_entries[l] += (double)E;
     lvl_parents[l] += (double)P;
     lvl_size[l] += (double)E;
     if (E == 0) return PGM_OK;
-    if (l == k - 1) {
+    if (l == k - 1 && !list_out) {
       return launch<kSum>(L, l, nullptr, nullptr, 0, nullptr, L.p_lo, L.p_hi, L.e_lo, "extend_sum",
                           (double)E);
     }
@@ -232,7 +306,10 @@ struct CliqueRun {
         nx.p_hi = eb - L.e_lo;
         nx.e_lo = 0;
         nx.e_hi = Tp;
-        PGM_TRY(level(l + 1, nx));
+        if (l + 1 == k)
+          PGM_TRY(emit(nx, Tp));
+        else
+          PGM_TRY(level(l + 1, nx));
       }
       pa = pb;
     }
@@ -241,6 +318,64 @@ struct CliqueRun {
 };
 
 }  // namespace
+
+// Rows for k = 1 (every vertex) and k = 2 (every DAG arc u -> v).
+__global__ void list_small_kernel(int32_t n, int k, const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
+                                  int32_t* __restrict__ out) {
+  for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n; u += (int64_t)gridDim.x * blockDim.x) {
+    if (k == 1) {
+      out[u] = (int32_t)u;
+    } else {
+      for (int32_t a = rp[u]; a < rp[u + 1]; a++) {
+        out[2 * (int64_t)a] = (int32_t)u;
+        out[2 * (int64_t)a + 1] = col[a];
+      }
+    }
+  }
+}
+
+pgm_status list_small(Graph& g, int k, int32_t* out) {
+  if (g.n == 0) return PGM_OK;
+  const int blocks = std::max(1, std::min(num_sms() * 8, (g.n + 255) / 256));
+  list_small_kernel<<<blocks, 256, 0, g.stream>>>(g.n, k, g.dag_rp, g.dag_col, out);
+  PGM_CHECK_LAUNCH();
+  return PGM_OK;
+}
+
+// Rows of the k-cliques of the whole graph into `out` (k IDs each, in DAG
+// order), by the level lists with the last level written; `rows` must be
+// the clique count.
+pgm_status list_kcliques(Graph& g, Workspace& ws, cudaStream_t s, int k, int32_t* out, int64_t rows) {
+  PGM_TRY(graph_orient(g));
+  PGM_TRY(graph_host_dag_rp(g));
+  PGM_TRY(ws.ctr.reserve(kSlots));
+  PGM_TRY_CUDA(cudaMemsetAsync(ws.ctr.p, 0, kSlots * sizeof(unsigned long long), s));
+  CliqueRun run(g, ws, s, k);
+  run.list_out = out;
+  Lvl L2;
+  L2.seg = g.dag_rp;
+  L2.seg32 = true;
+  L2.seg_shift = 0;
+  L2.vid = g.dag_col;
+  L2.h_seg = g.h_dag_rp.data();
+  L2.p_lo = 0;
+  L2.p_hi = g.n;
+  L2.e_lo = 0;
+  L2.e_hi = g.h_dag_rp[g.n];
+  PGM_TRY(run.level(2, L2));
+  unsigned long long h[kSlots];
+  bool deferred = false;
+  PGM_TRY(read_counters(ws.ctr.p, h, kSlots, s, &deferred));
+  if (h[kSlotErr]) {
+    set_error("list_kcliques: internal hub-list overflow");
+    return PGM_ENOMEM;
+  }
+  if (run.list_n != rows) {
+    set_error("list_kcliques: wrote %lld rows, expected %lld", (long long)run.list_n, (long long)rows);
+    return PGM_ECUDA;
+  }
+  return PGM_OK;
+}
 
 pgm_status count_kcliques(Graph& g, Workspace& ws, cudaStream_t s, int k, int32_t v_lo, int32_t v_hi,
                           uint64_t* out, unsigned long long* per_graph_dev) {
@@ -366,6 +501,46 @@ pgm_status pgm_count_kcliques_range(pgm_graph* g, int32_t k, int32_t v_lo, int32
   uint64_t c = 0;
   PGM_TRY(pgm::count_kcliques(g->g, g->g.ws, g->g.stream, k, v_lo, v_hi, &c, nullptr));
   *out_count = c;
+  return PGM_OK;
+}
+
+pgm_status pgm_list_kcliques(pgm_graph* g, int32_t k, int32_t* out_dev, int64_t cap_rows, int64_t* n_rows) {
+  if (!g || !n_rows || cap_rows < 0) {
+    pgm::set_error("pgm_list_kcliques: bad arguments");
+    return PGM_EINVAL;
+  }
+  if (k < 1 || k > pgm::kMaxK) {
+    pgm::set_error("pgm_list_kcliques: k=%d outside [1, %d]", k, pgm::kMaxK);
+    return PGM_EUNSUPPORTED;
+  }
+  pgm::Graph& G = g->g;
+  pgm::profiler().start(G.stream);
+  uint64_t total = 0;
+  PGM_TRY(pgm::count_kcliques(G, G.ws, G.stream, k, 0, G.n, &total, nullptr));
+  if (total > (uint64_t)INT64_MAX / (uint64_t)k) {
+    pgm::set_error("pgm_list_kcliques: %llu rows do not fit an index", (unsigned long long)total);
+    return PGM_EOVERFLOW;
+  }
+  if (!out_dev) {  // size query
+    *n_rows = (int64_t)total;
+    return PGM_OK;
+  }
+  if ((int64_t)total > cap_rows) {
+    *n_rows = (int64_t)total;
+    pgm::set_error("pgm_list_kcliques: %llu rows exceed the capacity of %lld", (unsigned long long)total,
+                   (long long)cap_rows);
+    return PGM_EOVERFLOW;
+  }
+  if (total > 0) {
+    if (k == 1 || k == 2) {
+      PGM_TRY(pgm::list_small(G, k, out_dev));
+    } else {
+      pgm::profiler().start(G.stream);
+      PGM_TRY(pgm::list_kcliques(G, G.ws, G.stream, k, out_dev, (int64_t)total));
+    }
+  }
+  PGM_TRY_CUDA(cudaStreamSynchronize(G.stream));
+  *n_rows = (int64_t)total;
   return PGM_OK;
 }
 

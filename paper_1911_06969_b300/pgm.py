@@ -96,6 +96,7 @@ _SIGS = {
     "pgm_graph_destroy": (None, [P]),
     "pgm_count_kcliques": (C.c_int, [P, C.c_int32, C.POINTER(C.c_uint64)]),
     "pgm_count_kcliques_range": (C.c_int, [P, C.c_int32, C.c_int32, C.c_int32, C.POINTER(C.c_uint64)]),
+    "pgm_list_kcliques": (C.c_int, [P, C.c_int32, P, C.c_int64, C.POINTER(C.c_int64)]),
     "pgm_count_motifs": (C.c_int, [P, C.c_int32, P, C.c_int32]),
     "pgm_count_motifs_range": (C.c_int, [P, C.c_int32, C.c_int32, C.c_int32, P, C.c_int32]),
     "pgm_batch_create": (C.c_int, [C.c_int32, P, P, P, C.c_uint32, P, C.POINTER(P)]),
@@ -205,6 +206,14 @@ def pgm_count_kcliques_range(g: int, k: int, v_lo: int, v_hi: int) -> int:
     out = C.c_uint64()
     _ok(load().pgm_count_kcliques_range(g, k, v_lo, v_hi, C.byref(out)), "pgm_count_kcliques_range")
     return int(out.value)
+
+
+def pgm_list_kcliques(g: int, k: int, out_dev_ptr: int = 0, cap_rows: int = 0) -> int:
+    """Rows of k vertex IDs (int32, row-major) into the device buffer at
+    out_dev_ptr; returns the number of k-cliques (out_dev_ptr = 0: size query)."""
+    n = C.c_int64()
+    _ok(load().pgm_list_kcliques(g, k, out_dev_ptr or None, cap_rows, C.byref(n)), "pgm_list_kcliques")
+    return int(n.value)
 
 
 def pgm_count_motifs(g: int, k: int) -> list:
