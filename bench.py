@@ -422,7 +422,31 @@ def extras(pgm, torch, stream, flush):
     finally:
         pgm.pgm_batch_destroy(h)
     out["serving_64_graphs"] = serving(pgm)
+    out["listing_triangles_rmat21"] = listing(pgm, torch)
     return out
+
+
+def listing(pgm, torch, k=3):
+    """Listing (next item after counting): every triangle of R-MAT 21 as a row
+    of 3 vertex IDs in a device buffer; the call counts, then writes."""
+    g = gg.rmat21()
+    h = pgm.pgm_graph_create_csr(g.n, g.rowptr, g.col)
+    try:
+        n = pgm.pgm_list_kcliques(h, k)
+        buf = torch.empty((n, k), dtype=torch.int32, device="cuda")
+        pgm.pgm_list_kcliques(h, k, buf.data_ptr(), n)  # warm-up
+        ts = []
+        for _ in range(2):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            pgm.pgm_list_kcliques(h, k, buf.data_ptr(), n)
+            torch.cuda.synchronize()
+            ts.append(time.perf_counter() - t0)
+        t = min(ts)
+        del buf
+        return {"k": k, "rows": n, "ms": t * 1e3, "rows_per_s": n / t, "bytes_written": n * k * 4}
+    finally:
+        pgm.pgm_graph_destroy(h)
 
 
 def serving(pgm, rate=2000.0, seconds=10.0, inflight=8, budget=60 << 30):
