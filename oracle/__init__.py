@@ -72,6 +72,8 @@ def _declare(lib):
     lib.orc_bf_motifs.argtypes = [I32, P, P, I32, P]
     lib.orc_clique_count.restype = I32
     lib.orc_clique_count.argtypes = [I32, P, P, I32, I32, I32, I32, I32, P]
+    lib.orc_p5_classes.restype = I32
+    lib.orc_p5_classes.argtypes = [P]
     lib.orc_esu_motifs.restype = I32
     lib.orc_esu_motifs.argtypes = [I32, P, P, I32, I32, I32, I32, P]
     lib.orc_formula_motifs_range.restype = I32
@@ -139,11 +141,22 @@ def bf_cliques(g, k: int) -> int:
     return int(out[0])
 
 
+def _npat(k: int) -> int:
+    return {3: 2, 4: 6, 5: 21}[k]
+
+
 def bf_motifs(g, k: int) -> list:
     rp, col = _arrs(g)
-    out = np.zeros(6, np.uint64)
+    out = np.zeros(21, np.uint64)
     _check(_L().orc_bf_motifs(g.n, rp.ctypes.data, col.ctypes.data, k, out.ctypes.data), "bf_motifs")
-    return [int(x) for x in out[: (2 if k == 3 else 6)]]
+    return [int(x) for x in out[: _npat(k)]]
+
+
+def p5_classes() -> list:
+    """Canonical 10-bit adjacency codes of the connected 5-vertex classes, in output order."""
+    codes = np.zeros(64, np.int32)
+    n = _L().orc_p5_classes(codes.ctypes.data)
+    return [int(x) for x in codes[:n]]
 
 
 def clique_levels(g, k: int, order: str = "id", roots=None, threads: int = 1) -> list:
@@ -164,10 +177,10 @@ def clique_count(g, k: int, order: str = "id", threads: int = 1) -> int:
 def esu_motifs(g, k: int, roots=None, threads: int = 1) -> list:
     rp, col = _arrs(g)
     lo, hi = (0, g.n) if roots is None else roots
-    out = np.zeros(6, np.uint64)
+    out = np.zeros(21, np.uint64)
     rc = _L().orc_esu_motifs(g.n, rp.ctypes.data, col.ctypes.data, k, lo, hi, threads, out.ctypes.data)
     _check(rc, "esu_motifs")
-    return [int(x) for x in out[: (2 if k == 3 else 6)]]
+    return [int(x) for x in out[: _npat(k)]]
 
 
 def formula_motifs(g, k: int, threads: int = 1) -> list:

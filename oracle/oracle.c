@@ -18,7 +18,12 @@
  *     counting, Sec. 2.1 and Sec. 3.2; support = count, Listing 4).
  * Motif output order (fixed here, since the paper's motif figure is not
  * available): k=3 -> [wedge, triangle]; k=4 -> [3-star, 4-path,
- * tailed-triangle, 4-cycle, diamond, 4-clique].
+ * tailed-triangle, 4-cycle, diamond, 4-clique]; k=5 -> the 21 connected
+ * graphs on 5 vertices ordered by edge count, then by the degree sequence
+ * (sorted non-increasing, compared lexicographically, smaller first), then
+ * by the canonical code (the smallest 10-bit adjacency code over the 120
+ * relabellings; bit i = pair i of (0,1),(0,2),(0,3),(0,4),(1,2),(1,3),
+ * (1,4),(2,3),(2,4),(3,4)).
  *
  * Tiers (all single-threaded unless `nthreads` > 1, in which case roots
  * are split across OpenMP threads and the integer partial sums added):
@@ -86,6 +91,104 @@ static int classify(int k, int edges, int maxdeg) {
 
 /* Exclusive prefix sum, the allocation step of inspection-execution
  * (Sec. 5.3): out[i] = sum of cnt[0..i-1]; out[len] = total. */
+/* --------------------------------------------- 5-vertex isomorphism classes */
+static const int P5[10][2] = {{0, 1}, {0, 2}, {0, 3}, {0, 4}, {1, 2}, {1, 3}, {1, 4}, {2, 3}, {2, 4}, {3, 4}};
+static int16_t g_p5_class[1024]; /* adjacency code -> class (-1: disconnected) */
+static int g_p5_ready = 0;
+
+static int p5_adj(int code, int a, int b) {
+  for (int i = 0; i < 10; i++)
+    if ((P5[i][0] == a && P5[i][1] == b) || (P5[i][0] == b && P5[i][1] == a)) return (code >> i) & 1;
+  return 0;
+}
+
+static int p5_connected(int code) {
+  int seen = 1, grew = 1;
+  while (grew) {
+    grew = 0;
+    for (int a = 0; a < 5; a++)
+      if (seen & (1 << a))
+        for (int b = 0; b < 5; b++)
+          if (!(seen & (1 << b)) && p5_adj(code, a, b)) {
+            seen |= 1 << b;
+            grew = 1;
+          }
+  }
+  return seen == 31;
+}
+
+/* smallest code over all 120 relabellings (perm[v] = new label of v) */
+static int p5_canon(int code) {
+  int best = 1 << 10, perm[5] = {0, 1, 2, 3, 4};
+  /* iterate permutations in lexicographic order */
+  for (;;) {
+    int c = 0;
+    for (int i = 0; i < 10; i++)
+      if (p5_adj(code, P5[i][0], P5[i][1])) {
+        int a = perm[P5[i][0]], b = perm[P5[i][1]];
+        for (int j = 0; j < 10; j++)
+          if ((P5[j][0] == a && P5[j][1] == b) || (P5[j][0] == b && P5[j][1] == a)) c |= 1 << j;
+      }
+    if (c < best) best = c;
+    int i = 3;
+    while (i >= 0 && perm[i] > perm[i + 1]) i--;
+    if (i < 0) break;
+    int j = 4;
+    while (perm[j] < perm[i]) j--;
+    int t = perm[i]; perm[i] = perm[j]; perm[j] = t;
+    for (int a = i + 1, b = 4; a < b; a++, b--) { t = perm[a]; perm[a] = perm[b]; perm[b] = t; }
+  }
+  return best;
+}
+
+/* sort key of a class: edges, then the degree sequence (non-increasing)
+ * lexicographically, then the canonical code */
+static void p5_key(int code, int key[7]) {
+  int deg[5] = {0, 0, 0, 0, 0}, e = 0;
+  for (int i = 0; i < 10; i++)
+    if ((code >> i) & 1) { deg[P5[i][0]]++; deg[P5[i][1]]++; e++; }
+  for (int a = 0; a < 5; a++)
+    for (int b = a + 1; b < 5; b++)
+      if (deg[b] > deg[a]) { int t = deg[a]; deg[a] = deg[b]; deg[b] = t; }
+  key[0] = e;
+  for (int a = 0; a < 5; a++) key[1 + a] = deg[a];
+  key[6] = code;
+}
+
+static int p5_key_cmp(const void *x, const void *y) {
+  int kx[7], ky[7];
+  p5_key(*(const int *)x, kx);
+  p5_key(*(const int *)y, ky);
+  for (int i = 0; i < 7; i++)
+    if (kx[i] != ky[i]) return kx[i] < ky[i] ? -1 : 1;
+  return 0;
+}
+
+static void p5_init(void) {
+  if (g_p5_ready) return;
+  int canon[1024], classes[64], nc = 0;
+  for (int c = 0; c < 1024; c++) {
+    canon[c] = p5_connected(c) ? p5_canon(c) : -1;
+    if (canon[c] >= 0 && canon[c] == c) classes[nc++] = c; /* a canonical code is its own class's minimum */
+  }
+  qsort(classes, (size_t)nc, sizeof(int), p5_key_cmp);
+  for (int c = 0; c < 1024; c++) {
+    g_p5_class[c] = -1;
+    for (int i = 0; i < nc; i++)
+      if (canon[c] == classes[i]) g_p5_class[c] = (int16_t)i;
+  }
+  g_p5_ready = 1;
+}
+
+/* number of classes and their canonical codes, in output order (tests) */
+int orc_p5_classes(int32_t *codes) {
+  p5_init();
+  int n = 0;
+  for (int c = 0; c < 1024; c++)
+    if (g_p5_class[c] >= 0 && p5_canon(c) == c) codes[g_p5_class[c]] = c, n++;
+  return n;
+}
+
 void orc_exclusive_scan(int64_t len, const int64_t *cnt, int64_t *out) {
   int64_t s = 0;
   for (int64_t i = 0; i < len; i++) {
@@ -145,10 +248,18 @@ static void bf_clique_visit(const uint64_t *adj, uint64_t set, void *ctx) {
   (*(uint64_t *)ctx)++;
 }
 
-typedef struct { int k; uint64_t cnt[6]; } bf_motif_ctx;
+typedef struct { int k; uint64_t cnt[21]; } bf_motif_ctx;
 static void bf_motif_visit(const uint64_t *adj, uint64_t set, void *vctx) {
   bf_motif_ctx *c = (bf_motif_ctx *)vctx;
   if (!connected_bits(adj, set)) return;
+  if (c->k == 5) {
+    int v[5], nv = 0, code = 0;
+    for (uint64_t s = set; s; s &= s - 1) v[nv++] = __builtin_ctzll(s);
+    for (int i = 0; i < 10; i++)
+      if ((adj[v[P5[i][0]]] >> v[P5[i][1]]) & 1) code |= 1 << i;
+    c->cnt[g_p5_class[code]]++;
+    return;
+  }
   int deg_sum = 0, maxdeg = 0;
   for (uint64_t s = set; s; s &= s - 1) {
     int d = popcount64(adj[__builtin_ctzll(s)] & set);
@@ -169,15 +280,16 @@ int orc_bf_cliques(int32_t n, const int64_t *rp, const int32_t *col, int32_t k, 
   return ORC_OK;
 }
 
-/* Motif counts by checking every k-subset (n <= 64, k in {3, 4}). */
+/* Motif counts by checking every k-subset (n <= 64, k in {3, 4, 5}). */
 int orc_bf_motifs(int32_t n, const int64_t *rp, const int32_t *col, int32_t k, uint64_t *out) {
   uint64_t adj[64];
-  if ((k != 3 && k != 4) || bits_from_csr(n, rp, col, adj)) return ORC_EINVAL;
+  if ((k < 3 || k > 5) || bits_from_csr(n, rp, col, adj)) return ORC_EINVAL;
+  p5_init();
   bf_motif_ctx c;
   memset(&c, 0, sizeof(c));
   c.k = k;
   if (k <= n) for_subsets(n, k, 0, 0, k, adj, bf_motif_visit, &c);
-  memcpy(out, c.cnt, sizeof(uint64_t) * (k == 3 ? 2 : 6));
+  memcpy(out, c.cnt, sizeof(uint64_t) * (k == 3 ? 2 : k == 4 ? 6 : 21));
   return ORC_OK;
 }
 
@@ -293,7 +405,7 @@ typedef struct {
   int32_t root;
   int32_t sub[8];
   int32_t nsub;
-  u128 cnt[6];
+  u128 cnt[21];
 } esu_ctx;
 
 static int in_list(const int32_t *a, int32_t len, int32_t x) {
@@ -303,6 +415,13 @@ static int in_list(const int32_t *a, int32_t len, int32_t x) {
 }
 
 static void esu_leaf(esu_ctx *c) {
+  if (c->k == 5) {
+    int code = 0;
+    for (int i = 0; i < 10; i++)
+      if (adjacent(c->rp, c->col, c->sub[P5[i][0]], c->sub[P5[i][1]])) code |= 1 << i;
+    c->cnt[g_p5_class[code]] += 1;
+    return;
+  }
   int deg[8] = {0}, edges = 0, maxdeg = 0;
   for (int i = 0; i < c->k; i++)
     for (int j = i + 1; j < c->k; j++)
@@ -352,12 +471,14 @@ static void esu_extend(esu_ctx *c, const int32_t *ext, int64_t next) {
   free(ext2);
 }
 
-/* Motif counts (k in {3, 4}) of the connected k-sets whose minimum vertex
+/* Motif counts (k in {3, 4, 5}) of the connected k-sets whose minimum vertex
  * lies in [root_lo, root_hi). */
 int orc_esu_motifs(int32_t n, const int64_t *rp, const int32_t *col, int32_t k, int32_t root_lo,
                    int32_t root_hi, int32_t nthreads, uint64_t *out) {
-  if ((k != 3 && k != 4) || root_lo < 0 || root_hi > n || root_lo > root_hi) return ORC_EINVAL;
-  u128 total[6];
+  if ((k < 3 || k > 5) || root_lo < 0 || root_hi > n || root_lo > root_hi) return ORC_EINVAL;
+  const int np = k == 3 ? 2 : k == 4 ? 6 : 21;
+  p5_init();
+  u128 total[21];
   memset(total, 0, sizeof(total));
   if (nthreads < 1) nthreads = 1;
 #pragma omp parallel num_threads(nthreads)
@@ -382,9 +503,9 @@ int orc_esu_motifs(int32_t n, const int64_t *rp, const int32_t *col, int32_t k, 
       free(ext);
     }
 #pragma omp critical
-    for (int p = 0; p < 6; p++) total[p] += c.cnt[p];
+    for (int p = 0; p < np; p++) total[p] += c.cnt[p];
   }
-  for (int p = 0; p < (k == 3 ? 2 : 6); p++) {
+  for (int p = 0; p < np; p++) {
     if (total[p] > (u128)UINT64_MAX) return ORC_EOVERFLOW;
     out[p] = (uint64_t)total[p];
   }

@@ -331,3 +331,70 @@ def test_pins_reject_planted_mistake(tmp_path, name, old, new):
     assert _pin_suite_passes(), "unmutated oracle must pass the compact pin suite"
     with oracle.use_variant(str(so)):
         assert not _pin_suite_passes(), f"pins did not catch: {name}"
+
+
+# ------------------------------------------------------------ 5-vertex motifs
+def test_p5_classes_known_census():
+    """There are 21 connected graphs on 5 vertices: 3 trees and 5, 5, 4, 2, 1, 1
+    graphs with 5..10 edges (the census of connected graphs)."""
+    from collections import Counter
+
+    codes = oracle.p5_classes()
+    assert len(codes) == 21 and len(set(codes)) == 21
+    assert sorted(Counter(bin(c).count("1") for c in codes).items()) == [
+        (4, 3), (5, 5), (6, 5), (7, 4), (8, 2), (9, 1), (10, 1)]
+
+
+def _p5_index(g5):
+    """Output index of a connected 5-vertex graph (its one count)."""
+    c = oracle.bf_motifs(g5, 5)
+    assert sum(c) == 1
+    return c.index(1)
+
+
+def test_p5_closed_forms():
+    import math
+
+    star_i = _p5_index(gg.star(4))
+    path_i = _p5_index(gg.path(5))
+    k5_i = _p5_index(gg.complete(5))
+    c5_i = _p5_index(gg.cycle(5))
+    k23_i = _p5_index(gg.complete_multipartite((2, 3)))
+    assert (path_i, star_i, c5_i, k5_i) == (0, 2, 3, 20)  # the order of the header comment
+    for n in (5, 6, 9, 12):
+        want = [0] * 21
+        want[k5_i] = math.comb(n, 5)
+        assert oracle.bf_motifs(gg.complete(n), 5) == want
+    for s in (4, 7, 11):
+        want = [0] * 21
+        want[star_i] = math.comb(s, 4)
+        assert oracle.bf_motifs(gg.star(s), 5) == want
+    for n in (6, 9, 20):
+        want = [0] * 21
+        want[path_i] = n
+        assert oracle.bf_motifs(gg.cycle(n), 5) == want
+    for n in (5, 8, 30):
+        want = [0] * 21
+        want[path_i] = n - 4
+        assert oracle.bf_motifs(gg.path(n), 5) == want
+    for a, b in ((2, 3), (3, 4), (4, 6), (5, 5)):
+        want = [0] * 21
+        want[star_i] = a * math.comb(b, 4) + b * math.comb(a, 4)
+        want[k23_i] = math.comb(a, 2) * math.comb(b, 3) + math.comb(a, 3) * math.comb(b, 2)
+        assert oracle.bf_motifs(gg.complete_multipartite((a, b)), 5) == want
+
+
+def test_p5_esu_agrees_with_brute_force():
+    for i in range(40):
+        g = gg.erdos_renyi(14 + i % 20, 0.12 + 0.02 * (i % 15), seed=900 + i)
+        assert oracle.esu_motifs(g, 5) == oracle.bf_motifs(g, 5), g.name
+    for g in (gg.barabasi_albert(60, 3, seed=3), gg.rmat(64, 300, seed=4)):
+        assert oracle.esu_motifs(g, 5) == oracle.bf_motifs(g, 5)
+
+
+def test_p5_relabel_invariance_and_roots():
+    g = gg.barabasi_albert(300, 4, seed=8)
+    perm = np.random.default_rng(1).permutation(g.n)
+    assert oracle.esu_motifs(gg.relabel(g, perm), 5) == oracle.esu_motifs(g, 5)
+    parts = [oracle.esu_motifs(g, 5, roots=r) for r in ((0, 100), (100, 101), (101, 300))]
+    assert [sum(x) for x in zip(*parts)] == oracle.esu_motifs(g, 5)
