@@ -179,6 +179,14 @@ pgm_status pgm_list_kcliques(pgm_graph* g, int32_t k, int32_t* out_dev, int64_t 
  * Sec. 3.2).  Output order:
  *   k = 3: [wedge, triangle]                                   (cap >= 2)
  *   k = 4: [3-star, 4-path, tailed-triangle, 4-cycle, diamond, 4-clique] (cap >= 6)
+ *   k = 5: the 21 connected 5-vertex graphs (cap >= 21), generic
+ *          classification by adjacency code, ordered by edge count, then
+ *          degree sequence (non-increasing, lexicographically smaller first),
+ *          then canonical code (the smallest 10-bit adjacency code over the
+ *          120 relabellings, bit i = pair i of (0,1),(0,2),(0,3),(0,4),(1,2),
+ *          (1,3),(1,4),(2,3),(2,4),(3,4)); index 0 = 5-path, 2 = 4-star,
+ *          3 = 5-cycle, 20 = 5-clique.  The levels are materialised as vertex
+ *          tuples: meant for graphs whose 4-vertex connected sets fit memory.
  * Other k: PGM_EUNSUPPORTED.  Requires n < 2^30. */
 pgm_status pgm_count_motifs(pgm_graph *g, int32_t k, uint64_t *out_counts, int32_t cap);
 

@@ -1005,13 +1005,17 @@ pgm_status count_motifs_on(Graph& g, Workspace& ws, cudaStream_t s, int k, int32
 
 pgm_status count_motifs(Graph& g, Workspace& ws, cudaStream_t s, int k, int32_t v_lo, int32_t v_hi,
                         uint64_t* out, unsigned long long* per_graph_dev) {
-  if (k != 3 && k != 4) {
-    set_error("count_motifs: k=%d unsupported (3 or 4)", k);
+  if (k < 3 || k > 5) {
+    set_error("count_motifs: k=%d unsupported (3, 4 or 5)", k);
     return PGM_EUNSUPPORTED;
   }
   if (v_lo < 0 || v_hi > g.n || v_lo > v_hi) {
     set_error("count_motifs: bad vertex range [%d, %d)", v_lo, v_hi);
     return PGM_EINVAL;
+  }
+  if (k == 5 && per_graph_dev) {
+    set_error("count_motifs: k=5 has no per-graph (batch) attribution");
+    return PGM_EUNSUPPORTED;
   }
   if (g.n >= (1 << 30)) {
     set_error("count_motifs: n=%d needs 30-bit vertex IDs", g.n);
@@ -1028,6 +1032,7 @@ pgm_status count_motifs(Graph& g, Workspace& ws, cudaStream_t s, int k, int32_t 
 
 pgm_status count_motifs_on(Graph& g, Workspace& ws, cudaStream_t s, int k, int32_t v_lo, int32_t v_hi,
                            uint64_t* out, unsigned long long* per_graph_dev) {
+  if (k == 5) return count_motifs5(g, ws, s, v_lo, v_hi, out);
   MotifRun run(g, ws, s, k);
   run.per_graph = per_graph_dev;
   PGM_TRY(run.prepare());
@@ -1086,16 +1091,15 @@ pgm_status pgm_count_motifs(pgm_graph* g, int32_t k, uint64_t* out_counts, int32
     pgm::set_error("pgm_count_motifs: null argument");
     return PGM_EINVAL;
   }
-  if (k == 3 || k == 4) {
-    if ((k == 3 && cap < 2) || (k == 4 && cap < 6)) {
-      pgm::set_error("pgm_count_motifs: output capacity %d too small for k=%d", cap, k);
-      return PGM_EINVAL;
-    }
+  const int np = k == 3 ? 2 : k == 4 ? 6 : k == 5 ? 21 : 0;
+  if (np && cap < np) {
+    pgm::set_error("pgm_count_motifs: output capacity %d too small for k=%d", cap, k);
+    return PGM_EINVAL;
   }
   pgm::profiler().start(g->g.stream);
-  uint64_t c[6] = {0, 0, 0, 0, 0, 0};
+  uint64_t c[21] = {0};
   PGM_TRY(pgm::count_motifs(g->g, g->g.ws, g->g.stream, k, 0, g->g.n, c, nullptr));
-  memcpy(out_counts, c, sizeof(uint64_t) * (k == 3 ? 2 : 6));
+  memcpy(out_counts, c, sizeof(uint64_t) * np);
   return PGM_OK;
 }
 
@@ -1105,14 +1109,15 @@ pgm_status pgm_count_motifs_range(pgm_graph* g, int32_t k, int32_t v_lo, int32_t
     pgm::set_error("pgm_count_motifs_range: null argument");
     return PGM_EINVAL;
   }
-  if ((k == 3 && cap < 2) || (k == 4 && cap < 6)) {
+  const int np = k == 3 ? 2 : k == 4 ? 6 : k == 5 ? 21 : 0;
+  if (np && cap < np) {
     pgm::set_error("pgm_count_motifs_range: output capacity too small");
     return PGM_EINVAL;
   }
   pgm::profiler().start(g->g.stream);
-  uint64_t c[6] = {0, 0, 0, 0, 0, 0};
+  uint64_t c[21] = {0};
   PGM_TRY(pgm::count_motifs(g->g, g->g.ws, g->g.stream, k, v_lo, v_hi, c, nullptr));
-  memcpy(out_counts, c, sizeof(uint64_t) * (k == 3 ? 2 : 6));
+  memcpy(out_counts, c, sizeof(uint64_t) * np);
   return PGM_OK;
 }
 

@@ -216,16 +216,20 @@ def pgm_list_kcliques(g: int, k: int, out_dev_ptr: int = 0, cap_rows: int = 0) -
     return int(n.value)
 
 
+def _npat(k: int) -> int:
+    return {3: 2, 4: 6, 5: 21}.get(k, 0)
+
+
 def pgm_count_motifs(g: int, k: int) -> list:
-    out = np.zeros(6, np.uint64)
-    _ok(load().pgm_count_motifs(g, k, out.ctypes.data, 6), "pgm_count_motifs")
-    return [int(x) for x in out[: (2 if k == 3 else 6)]]
+    out = np.zeros(21, np.uint64)
+    _ok(load().pgm_count_motifs(g, k, out.ctypes.data, 21), "pgm_count_motifs")
+    return [int(x) for x in out[: _npat(k)]]
 
 
 def pgm_count_motifs_range(g: int, k: int, v_lo: int, v_hi: int) -> list:
-    out = np.zeros(6, np.uint64)
-    _ok(load().pgm_count_motifs_range(g, k, v_lo, v_hi, out.ctypes.data, 6), "pgm_count_motifs_range")
-    return [int(x) for x in out[: (2 if k == 3 else 6)]]
+    out = np.zeros(21, np.uint64)
+    _ok(load().pgm_count_motifs_range(g, k, v_lo, v_hi, out.ctypes.data, 21), "pgm_count_motifs_range")
+    return [int(x) for x in out[: _npat(k)]]
 
 
 # ----------------------------------------------------------------- batches
