@@ -185,8 +185,8 @@ pgm_status pgm_list_kcliques(pgm_graph* g, int32_t k, int32_t* out_dev, int64_t 
  *          then canonical code (the smallest 10-bit adjacency code over the
  *          120 relabellings, bit i = pair i of (0,1),(0,2),(0,3),(0,4),(1,2),
  *          (1,3),(1,4),(2,3),(2,4),(3,4)); index 0 = 5-path, 2 = 4-star,
- *          3 = 5-cycle, 20 = 5-clique.  The levels are materialised as vertex
- *          tuples: meant for graphs whose 4-vertex connected sets fit memory.
+ *          3 = 5-cycle, 20 = 5-clique.  Levels 3 and 4 are materialised as
+ *          vertex tuples, in chunks of at most level_budget / 8 entries.
  * Other k: PGM_EUNSUPPORTED.  Requires n < 2^30. */
 pgm_status pgm_count_motifs(pgm_graph *g, int32_t k, uint64_t *out_counts, int32_t cap);
 
@@ -194,6 +194,20 @@ pgm_status pgm_count_motifs(pgm_graph *g, int32_t k, uint64_t *out_counts, int32
  * lies in [v_lo, v_hi); additive over a partition of [0, n). */
 pgm_status pgm_count_motifs_range(pgm_graph *g, int32_t k, int32_t v_lo, int32_t v_hi,
                                   uint64_t *out_counts, int32_t cap);
+
+/* List the connected k-vertex sets (k = 3, 4, 5; Sec. 3.3 Listing 4 with
+ * the last level written instead of reduced, Sec. 5.1).  Writes one row of
+ * k + 1 int32 per set into the caller's DEVICE buffer out_dev (cap_rows *
+ * (k + 1) entries, row-major): the k vertex IDs in the breadth-first
+ * canonical order of the set (first the minimum ID, then each next vertex
+ * the unused one adjacent to the prefix with the smallest (index of its
+ * first neighbour in the prefix, ID)), then the pattern index in the order
+ * of pgm_count_motifs.  Rows appear in no particular order.  *n_rows
+ * receives the number of sets (the sum of the motif counts).  out_dev =
+ * NULL is a size query; PGM_EOVERFLOW (with *n_rows set) if the sets
+ * exceed cap_rows, nothing written then.  Other k: PGM_EUNSUPPORTED.
+ * Requires n < 2^30. */
+pgm_status pgm_list_motifs(pgm_graph *g, int32_t k, int32_t *out_dev, int64_t cap_rows, int64_t *n_rows);
 
 /* --------------------------------------------------------------- batches */
 

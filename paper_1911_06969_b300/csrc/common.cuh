@@ -161,6 +161,9 @@ pgm_status graph_host_dag_rp(Graph& g);
 pgm_status graph_dag_arcs(Graph& g, int32_t v_lo, int32_t v_hi, int64_t* arcs);
 // 5-motif counts (21 classes) of the connected 5-sets whose minimum vertex is in [v_lo, v_hi)
 pgm_status count_motifs5(Graph& g, Workspace& ws, cudaStream_t s, int32_t v_lo, int32_t v_hi, uint64_t* out);
+// rows of k IDs (canonical order) + class of every connected k-set, k = 3..5, into out_dev
+pgm_status list_motifs(Graph& g, Workspace& ws, cudaStream_t s, int k, int32_t* out_dev, int64_t cap_rows,
+                       int64_t* n_rows);
 // motif count on exactly this graph's IDs (count_motifs may switch to a relabelled copy)
 pgm_status count_motifs_on(Graph& g, Workspace& ws, cudaStream_t s, int k, int32_t v_lo, int32_t v_hi,
                            uint64_t* out, unsigned long long* per_graph_dev);

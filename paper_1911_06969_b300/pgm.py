@@ -97,6 +97,7 @@ _SIGS = {
     "pgm_count_kcliques": (C.c_int, [P, C.c_int32, C.POINTER(C.c_uint64)]),
     "pgm_count_kcliques_range": (C.c_int, [P, C.c_int32, C.c_int32, C.c_int32, C.POINTER(C.c_uint64)]),
     "pgm_list_kcliques": (C.c_int, [P, C.c_int32, P, C.c_int64, C.POINTER(C.c_int64)]),
+    "pgm_list_motifs": (C.c_int, [P, C.c_int32, P, C.c_int64, C.POINTER(C.c_int64)]),
     "pgm_count_motifs": (C.c_int, [P, C.c_int32, P, C.c_int32]),
     "pgm_count_motifs_range": (C.c_int, [P, C.c_int32, C.c_int32, C.c_int32, P, C.c_int32]),
     "pgm_batch_create": (C.c_int, [C.c_int32, P, P, P, C.c_uint32, P, C.POINTER(P)]),
@@ -213,6 +214,15 @@ def pgm_list_kcliques(g: int, k: int, out_dev_ptr: int = 0, cap_rows: int = 0) -
     out_dev_ptr; returns the number of k-cliques (out_dev_ptr = 0: size query)."""
     n = C.c_int64()
     _ok(load().pgm_list_kcliques(g, k, out_dev_ptr or None, cap_rows, C.byref(n)), "pgm_list_kcliques")
+    return int(n.value)
+
+
+def pgm_list_motifs(g: int, k: int, out_dev_ptr: int = 0, cap_rows: int = 0) -> int:
+    """Rows of k vertex IDs (canonical order) + pattern index (int32, row-major,
+    k + 1 per row) into the device buffer at out_dev_ptr; returns the number of
+    connected k-sets (out_dev_ptr = 0: size query)."""
+    n = C.c_int64()
+    _ok(load().pgm_list_motifs(g, k, out_dev_ptr or None, cap_rows, C.byref(n)), "pgm_list_motifs")
     return int(n.value)
 
 
