@@ -172,6 +172,17 @@ pgm_status pgm_count_kcliques_range(pgm_graph *g, int32_t k, int32_t v_lo, int32
  * *n_rows set) if the cliques exceed cap_rows; nothing is written then. */
 pgm_status pgm_list_kcliques(pgm_graph* g, int32_t k, int32_t* out_dev, int64_t cap_rows, int64_t* n_rows);
 
+/* pgm_list_kcliques with the rows written to a HOST buffer out_host
+ * (cap_rows * k int32), for listings larger than device memory (the
+ * edge-blocking of Sec. 5.2 carried to the output).  The last level of each
+ * chunk is emitted into one of two device staging buffers of
+ * max(min(level_budget, 2^26), d+_max) rows and copied out while the other
+ * fills, so device memory beyond the graph stays bounded.  Page-locked host
+ * memory lets the copies overlap the listing; pageable memory works,
+ * slower.  Rows are in chunk order; same size query, overflow and k rules
+ * as pgm_list_kcliques. */
+pgm_status pgm_list_kcliques_host(pgm_graph* g, int32_t k, int32_t* out_host, int64_t cap_rows, int64_t* n_rows);
+
 /* Vertex-induced motif counts (Sec. 2.2; Sec. 3.3 Listing 4 "motif
  * counting"; customised classification Sec. 4.2, Listing 6): for each
  * connected k-vertex pattern, the number of vertex sets whose induced

@@ -85,6 +85,74 @@ __global__ void emit_kernel(EmitArgs A) {
   }
 }
 
+// Rows streamed to host memory: the last level of every edge-blocking chunk
+// is emitted into one of two device staging buffers; a full buffer is
+// copied to the host on a copy stream while the counting stream fills the
+// other.  Chunks are cut so that one chunk's rows fit a staging buffer;
+// device memory stays bounded by the staging size whatever the number of
+// rows.
+struct HostSink {
+  int32_t* host = nullptr;  // caller's rows
+  int64_t cap_rows = 0;     // rows per staging buffer
+  int64_t written = 0;      // rows already copied (or being copied) to the host
+  int64_t fill = 0;         // rows in the current staging buffer
+  int cur = 0;
+  int32_t* buf[2] = {nullptr, nullptr};
+  cudaStream_t copy = nullptr;
+  cudaEvent_t filled[2] = {nullptr, nullptr};  // on the counting stream: buffer's rows written
+  cudaEvent_t done[2] = {nullptr, nullptr};    // on the copy stream: buffer copied out
+  int k = 0;
+
+  pgm_status init(int k_, int64_t rows) {
+    k = k_;
+    cap_rows = rows;
+    PGM_TRY_CUDA(cudaStreamCreateWithFlags(&copy, cudaStreamNonBlocking));
+    for (int b = 0; b < 2; b++) {
+      PGM_TRY_CUDA(cudaMalloc(&buf[b], (size_t)rows * k * sizeof(int32_t)));
+      PGM_TRY_CUDA(cudaEventCreateWithFlags(&filled[b], cudaEventDisableTiming));
+      PGM_TRY_CUDA(cudaEventCreateWithFlags(&done[b], cudaEventDisableTiming));
+    }
+    return PGM_OK;
+  }
+  // hand the current buffer to the copy stream; the counting stream then
+  // writes the other one once its previous copy has finished
+  pgm_status flush(cudaStream_t s) {
+    if (fill > 0) {
+      PGM_TRY_CUDA(cudaEventRecord(filled[cur], s));
+      PGM_TRY_CUDA(cudaStreamWaitEvent(copy, filled[cur], 0));
+      PGM_TRY_CUDA(cudaMemcpyAsync(host + written * k, buf[cur], (size_t)fill * k * sizeof(int32_t),
+                                   cudaMemcpyDeviceToHost, copy));
+      PGM_TRY_CUDA(cudaEventRecord(done[cur], copy));
+      written += fill;
+      fill = 0;
+      cur ^= 1;
+      PGM_TRY_CUDA(cudaStreamWaitEvent(s, done[cur], 0));  // no-op before the buffer's first copy
+    }
+    return PGM_OK;
+  }
+  pgm_status finish() {
+    if (copy) PGM_TRY_CUDA(cudaStreamSynchronize(copy));
+    return PGM_OK;
+  }
+  // staging space for n more rows (n <= cap_rows)
+  pgm_status reserve(int64_t n, cudaStream_t s) {
+    if (fill + n > cap_rows) PGM_TRY(flush(s));
+    return PGM_OK;
+  }
+  void release() {
+    if (copy) cudaStreamSynchronize(copy);
+    for (int b = 0; b < 2; b++) {
+      if (buf[b]) cudaFree(buf[b]);
+      if (filled[b]) cudaEventDestroy(filled[b]);
+      if (done[b]) cudaEventDestroy(done[b]);
+      buf[b] = nullptr;
+      filled[b] = done[b] = nullptr;
+    }
+    if (copy) cudaStreamDestroy(copy);
+    copy = nullptr;
+  }
+};
+
 // counter slots in ws.ctr
 constexpr int kSlotQueue = 0;  // 4 per launch (reset per launch)
 constexpr int kSlotErr = 15;   // hub-list overflow counter
@@ -105,6 +173,8 @@ struct CliqueRun {
   // listing mode (list_out != nullptr): the last level is written and emitted
   int32_t* list_out = nullptr;
   int64_t list_n = 0;
+  HostSink* sink = nullptr;  // rows streamed to the host (list_out unused then)
+  int64_t budget;            // entries per edge-blocking chunk
   Lvl chain[Workspace::kMaxLevels + 1];
   double lvl_parents[Workspace::kMaxLevels] = {0};
   double lvl_size[Workspace::kMaxLevels + 4] = {0};
@@ -114,6 +184,7 @@ struct CliqueRun {
     cap = o.warp_stage_cap;
     hub = o.hub_threshold > 0 ? std::min(o.hub_threshold, cap) : cap;
     block_cap = 12288;  // ints staged per block (48 KB: four 512-thread blocks per SM)
+    budget = o.level_budget;
   }
 
   unsigned long long* ctr() { return ws.ctr.p; }
@@ -225,6 +296,16 @@ struct CliqueRun {
     A.n = n;
     A.out = list_out;
     A.out_base = list_n;
+    if (sink) {
+      if (n > sink->cap_rows) {
+        set_error("list_kcliques: %lld rows of one chunk exceed the staging buffer", (long long)n);
+        return PGM_ENOMEM;
+      }
+      PGM_TRY(sink->reserve(n, s));
+      A.out = sink->buf[sink->cur];
+      A.out_base = sink->fill;
+      sink->fill += n;
+    }
     Profiler& prof = profiler();
     int id = prof.begin("extend_list", k);
     const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)num_sms() * 8, (n + 255) / 256));
@@ -243,7 +324,7 @@ struct CliqueRun {
     lvl_parents[l] += (double)P;
     lvl_size[l] += (double)E;
     if (E == 0) return PGM_OK;
-    if (l == k - 1 && !list_out) {
+    if (l == k - 1 && !list_out && !sink) {
       return launch<kSum>(L, l, nullptr, nullptr, 0, nullptr, L.p_lo, L.p_hi, L.e_lo, "extend_sum",
                           (double)E);
     }
@@ -261,7 +342,8 @@ struct CliqueRun {
     int64_t T = 0;
     PGM_TRY(read_dev(ws.off[l].p + E, &T, s));
     if (T == 0) return PGM_OK;
-    const int64_t B = o.level_budget;
+    // with rows streamed to the host, the chunks of the last level fit a staging buffer
+    const int64_t B = sink && l == k - 1 ? std::min<int64_t>(budget, sink->cap_rows) : budget;
     int64_t pa = L.p_lo;
     while (pa < L.p_hi) {
       int64_t ea, pb, eb;
@@ -345,13 +427,15 @@ pgm_status list_small(Graph& g, int k, int32_t* out) {
 // Rows of the k-cliques of the whole graph into `out` (k IDs each, in DAG
 // order), by the level lists with the last level written; `rows` must be
 // the clique count.
-pgm_status list_kcliques(Graph& g, Workspace& ws, cudaStream_t s, int k, int32_t* out, int64_t rows) {
+pgm_status list_kcliques(Graph& g, Workspace& ws, cudaStream_t s, int k, int32_t* out, int64_t rows,
+                         HostSink* sink) {
   PGM_TRY(graph_orient(g));
   PGM_TRY(graph_host_dag_rp(g));
   PGM_TRY(ws.ctr.reserve(kSlots));
   PGM_TRY_CUDA(cudaMemsetAsync(ws.ctr.p, 0, kSlots * sizeof(unsigned long long), s));
   CliqueRun run(g, ws, s, k);
   run.list_out = out;
+  run.sink = sink;
   Lvl L2;
   L2.seg = g.dag_rp;
   L2.seg32 = true;
@@ -373,6 +457,10 @@ pgm_status list_kcliques(Graph& g, Workspace& ws, cudaStream_t s, int k, int32_t
   if (run.list_n != rows) {
     set_error("list_kcliques: wrote %lld rows, expected %lld", (long long)run.list_n, (long long)rows);
     return PGM_ECUDA;
+  }
+  if (sink) {
+    PGM_TRY(sink->flush(s));
+    PGM_TRY(sink->finish());
   }
   return PGM_OK;
 }
@@ -504,13 +592,14 @@ pgm_status pgm_count_kcliques_range(pgm_graph* g, int32_t k, int32_t v_lo, int32
   return PGM_OK;
 }
 
-pgm_status pgm_list_kcliques(pgm_graph* g, int32_t k, int32_t* out_dev, int64_t cap_rows, int64_t* n_rows) {
+static pgm_status list_kcliques_to(pgm_graph* g, int32_t k, int32_t* out, int64_t cap_rows, int64_t* n_rows,
+                                   bool host, const char* name) {
   if (!g || !n_rows || cap_rows < 0) {
-    pgm::set_error("pgm_list_kcliques: bad arguments");
+    pgm::set_error("%s: bad arguments", name);
     return PGM_EINVAL;
   }
   if (k < 1 || k > pgm::kMaxK) {
-    pgm::set_error("pgm_list_kcliques: k=%d outside [1, %d]", k, pgm::kMaxK);
+    pgm::set_error("%s: k=%d outside [1, %d]", name, k, pgm::kMaxK);
     return PGM_EUNSUPPORTED;
   }
   pgm::Graph& G = g->g;
@@ -518,30 +607,59 @@ pgm_status pgm_list_kcliques(pgm_graph* g, int32_t k, int32_t* out_dev, int64_t 
   uint64_t total = 0;
   PGM_TRY(pgm::count_kcliques(G, G.ws, G.stream, k, 0, G.n, &total, nullptr));
   if (total > (uint64_t)INT64_MAX / (uint64_t)k) {
-    pgm::set_error("pgm_list_kcliques: %llu rows do not fit an index", (unsigned long long)total);
+    pgm::set_error("%s: %llu rows do not fit an index", name, (unsigned long long)total);
     return PGM_EOVERFLOW;
   }
-  if (!out_dev) {  // size query
-    *n_rows = (int64_t)total;
-    return PGM_OK;
-  }
+  *n_rows = (int64_t)total;
+  if (!out) return PGM_OK;  // size query
   if ((int64_t)total > cap_rows) {
-    *n_rows = (int64_t)total;
-    pgm::set_error("pgm_list_kcliques: %llu rows exceed the capacity of %lld", (unsigned long long)total,
-                   (long long)cap_rows);
+    pgm::set_error("%s: %llu rows exceed the capacity of %lld", name, (unsigned long long)total, (long long)cap_rows);
     return PGM_EOVERFLOW;
   }
-  if (total > 0) {
+  if (total == 0) return PGM_OK;
+  if (!host) {
     if (k == 1 || k == 2) {
-      PGM_TRY(pgm::list_small(G, k, out_dev));
+      PGM_TRY(pgm::list_small(G, k, out));
     } else {
       pgm::profiler().start(G.stream);
-      PGM_TRY(pgm::list_kcliques(G, G.ws, G.stream, k, out_dev, (int64_t)total));
+      PGM_TRY(pgm::list_kcliques(G, G.ws, G.stream, k, out, (int64_t)total, nullptr));
     }
+    PGM_TRY_CUDA(cudaStreamSynchronize(G.stream));
+    return PGM_OK;
   }
-  PGM_TRY_CUDA(cudaStreamSynchronize(G.stream));
-  *n_rows = (int64_t)total;
-  return PGM_OK;
+  pgm_status st = PGM_OK;
+  if (k == 1 || k == 2) {
+    // n or m rows: no larger than the graph itself
+    int32_t* tmp = nullptr;
+    PGM_TRY_CUDA(cudaMalloc(&tmp, (size_t)total * k * sizeof(int32_t)));
+    st = pgm::list_small(G, k, tmp);
+    if (st == PGM_OK && cudaMemcpyAsync(out, tmp, (size_t)total * k * sizeof(int32_t), cudaMemcpyDeviceToHost,
+                                        G.stream) != cudaSuccess)
+      st = PGM_ECUDA;
+    if (cudaStreamSynchronize(G.stream) != cudaSuccess && st == PGM_OK) st = PGM_ECUDA;
+    cudaFree(tmp);
+    if (st == PGM_ECUDA) pgm::set_error("%s: copy to the host failed: %s", name, cudaGetErrorString(cudaGetLastError()));
+    return st;
+  }
+  pgm::HostSink sink;
+  sink.host = out;
+  const int64_t staging = std::max<int64_t>(std::min<int64_t>(pgm::options().level_budget, (int64_t)1 << 26), G.dag_dmax);
+  st = sink.init(k, staging);
+  if (st == PGM_OK) {
+    pgm::profiler().start(G.stream);
+    st = pgm::list_kcliques(G, G.ws, G.stream, k, nullptr, (int64_t)total, &sink);
+  }
+  cudaStreamSynchronize(G.stream);
+  sink.release();
+  return st;
+}
+
+pgm_status pgm_list_kcliques(pgm_graph* g, int32_t k, int32_t* out_dev, int64_t cap_rows, int64_t* n_rows) {
+  return list_kcliques_to(g, k, out_dev, cap_rows, n_rows, false, "pgm_list_kcliques");
+}
+
+pgm_status pgm_list_kcliques_host(pgm_graph* g, int32_t k, int32_t* out_host, int64_t cap_rows, int64_t* n_rows) {
+  return list_kcliques_to(g, k, out_host, cap_rows, n_rows, true, "pgm_list_kcliques_host");
 }
 
 }  // extern "C"

@@ -98,6 +98,7 @@ _SIGS = {
     "pgm_count_kcliques_range": (C.c_int, [P, C.c_int32, C.c_int32, C.c_int32, C.POINTER(C.c_uint64)]),
     "pgm_list_kcliques": (C.c_int, [P, C.c_int32, P, C.c_int64, C.POINTER(C.c_int64)]),
     "pgm_list_motifs": (C.c_int, [P, C.c_int32, P, C.c_int64, C.POINTER(C.c_int64)]),
+    "pgm_list_kcliques_host": (C.c_int, [P, C.c_int32, P, C.c_int64, C.POINTER(C.c_int64)]),
     "pgm_count_motifs": (C.c_int, [P, C.c_int32, P, C.c_int32]),
     "pgm_count_motifs_range": (C.c_int, [P, C.c_int32, C.c_int32, C.c_int32, P, C.c_int32]),
     "pgm_batch_create": (C.c_int, [C.c_int32, P, P, P, C.c_uint32, P, C.POINTER(P)]),
@@ -214,6 +215,21 @@ def pgm_list_kcliques(g: int, k: int, out_dev_ptr: int = 0, cap_rows: int = 0) -
     out_dev_ptr; returns the number of k-cliques (out_dev_ptr = 0: size query)."""
     n = C.c_int64()
     _ok(load().pgm_list_kcliques(g, k, out_dev_ptr or None, cap_rows, C.byref(n)), "pgm_list_kcliques")
+    return int(n.value)
+
+
+def pgm_list_kcliques_host(g: int, k: int, out=None) -> int:
+    """Rows of k vertex IDs into the host array ``out`` (int32, shape (rows, k),
+    C-contiguous; page-locked memory lets the copies overlap); returns the
+    number of k-cliques (out = None: size query)."""
+    n = C.c_int64()
+    if out is None:
+        _ok(load().pgm_list_kcliques_host(g, k, None, 0, C.byref(n)), "pgm_list_kcliques_host")
+    else:
+        if out.dtype != np.int32 or not out.flags["C_CONTIGUOUS"] or (out.ndim == 2 and out.shape[1] != k):
+            raise ValueError("out must be a C-contiguous int32 array of shape (rows, k)")
+        _ok(load().pgm_list_kcliques_host(g, k, out.ctypes.data, out.size // max(k, 1), C.byref(n)),
+            "pgm_list_kcliques_host")
     return int(n.value)
 
 

@@ -83,6 +83,36 @@ def test_list_chunked_and_overflow():
         pgm.pgm_graph_destroy(h)
 
 
+def test_list_kcliques_to_host():
+    """Rows streamed to host memory through the staging buffers equal the
+    device listing; a small level budget forces many chunks and flushes."""
+    import torch
+
+    g = gg.barabasi_albert(1500, 9, seed=34)
+    defaults = pgm.pgm_get_options()
+    h = pgm.pgm_graph_create_csr(g.n, g.rowptr, g.col)
+    try:
+        for k in (1, 2, 3, 4, 5):
+            dev = list_rows(g, k)
+            n = pgm.pgm_list_kcliques_host(h, k)
+            out = np.full((n, k), -1, np.int32)
+            assert pgm.pgm_list_kcliques_host(h, k, out) == n == len(dev)
+            assert sorted(map(tuple, out)) == sorted(map(tuple, dev)), k
+        pgm.pgm_set_options(level_budget=1024)
+        for k in (3, 4):
+            n = pgm.pgm_list_kcliques_host(h, k)
+            out = torch.full((n, k), -1, dtype=torch.int32).pin_memory().numpy()
+            assert pgm.pgm_list_kcliques_host(h, k, out) == n == oracle.clique_count(g, k, "degree")
+            check_rows(g, k, out)
+        small = np.zeros((n - 1, 4), np.int32)
+        with pytest.raises(pgm.PgmError) as e:
+            pgm.pgm_list_kcliques_host(h, 4, small)
+        assert e.value.status == pgm.PGM_EOVERFLOW
+    finally:
+        pgm.pgm_set_options(**defaults)
+        pgm.pgm_graph_destroy(h)
+
+
 # ------------------------------------------------------------ motif listing
 PAIRS = [(0, 1), (0, 2), (0, 3), (0, 4), (1, 2), (1, 3), (1, 4), (2, 3), (2, 4), (3, 4)]
 
