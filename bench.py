@@ -178,7 +178,9 @@ def main(argv=None):
     ap.add_argument("--clique-engine", type=int, default=0, choices=[0, 1, 2],
                     help="profiling: 0 auto, 1 level lists, 2 bitset levels")
     ap.add_argument("--motif-only", type=int, default=0, metavar="N",
-                    help="profiling: time only 4-motif counting on a Chung-Lu graph of N vertices")
+                    help="profiling: time only motif counting (--motif-k) on a graph of N vertices")
+    ap.add_argument("--motif-k", type=int, default=4, choices=[3, 4, 5],
+                    help="profiling: motif size of --motif-only (3, 4: Chung-Lu graph; 5: G(N, 10/(N-1)))")
     args = ap.parse_args(argv)
     if args.impl == "reference":
         return run_reference(args)
@@ -309,29 +311,32 @@ def main(argv=None):
 
 
 def motif_only(args):
-    """4-motif counting alone on a Chung-Lu graph (exponent 2.1, mean weight
-    10, weights capped at 20,000) of --motif-only vertices: a small case of
-    the motif kernels for profiling."""
+    """Motif counting alone, for profiling: k = 3, 4 on a Chung-Lu graph
+    (exponent 2.1, mean weight 10, weights capped at 20,000) of --motif-only
+    vertices; k = 5 on an Erdos-Renyi graph G(n, 10 / (n - 1))."""
     import torch
 
     from paper_1911_06969_b300 import pgm
 
-    n = args.motif_only
-    g = gg.chung_lu_1m() if n == 1 << 20 else gg.chung_lu(n, 2.1, 10.0, 20000.0, 1)
+    n, k = args.motif_only, args.motif_k
+    if k == 5:
+        g = gg.erdos_renyi(n, 10.0 / (n - 1), 1)
+    else:
+        g = gg.chung_lu_1m() if n == 1 << 20 else gg.chung_lu(n, 2.1, 10.0, 20000.0, 1)
     stream = torch.cuda.Stream()
     with pgm.Graph(g, stream=stream) as G:
         for _ in range(args.warmup):
-            m4 = G.motifs(4)
+            mk = G.motifs(k)
         ms = []
         for _ in range(args.steps):
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            m4 = G.motifs(4)
+            mk = G.motifs(k)
             e1.record(stream)
             e1.synchronize()
             ms.append(e0.elapsed_time(e1))
-    print(json.dumps({"workload": f"4-motif count, Chung-Lu n={n}", "n": g.n, "m": g.m, "counts": m4,
+    print(json.dumps({"workload": f"{k}-motif count, {g.name}", "n": g.n, "m": g.m, "counts": mk,
                       "ms": [round(x, 3) for x in ms]}), flush=True)
     return 0
 
@@ -423,7 +428,23 @@ def extras(pgm, torch, stream, flush):
         pgm.pgm_batch_destroy(h)
     out["serving_64_graphs"] = serving(pgm)
     out["listing_triangles_rmat21"] = listing(pgm, torch)
+    out["motif5_ba20k"] = motif5(pgm)
     return out
+
+
+def motif5(pgm):
+    """5-motif counting (21 classes, generic engine) on a Barabasi-Albert graph
+    n = 20,000, m = 4: classified connected 5-sets per second."""
+    g = gg.barabasi_albert(20000, 4, seed=2)
+    with pgm.Graph(g) as G:
+        c = G.motifs(5)
+        ts = []
+        for _ in range(3):
+            t0 = time.perf_counter()
+            c = G.motifs(5)
+            ts.append(time.perf_counter() - t0)
+    t = min(ts)
+    return {"graph": g.name, "sets": sum(c), "ms": t * 1e3, "sets_per_s": sum(c) / t, "counts": c}
 
 
 def host_mem_available() -> int:

@@ -164,6 +164,19 @@ __device__ __forceinline__ int32_t pick(const int32_t (&a)[N], int j) {
   return r;
 }
 
+// x in a[0, len): branch-free binary search whose trip count depends only on
+// len, so a warp searching one list for 32 keys does not diverge
+__device__ __forceinline__ bool member_u(const int32_t* __restrict__ a, int len, int32_t x) {
+  if (len <= 0) return false;
+  int lo = 0;
+  for (int n = len; n > 1;) {
+    const int half = n >> 1;
+    lo = __ldg(a + lo + half) <= x ? lo + half : lo;
+    n -= half;
+  }
+  return __ldg(a + lo) == x;
+}
+
 // one warp per entry of a level of I-vertex tuples
 template <int MODE, int I>
 __global__ void __launch_bounds__(256) mg_extend(MgArgs A) {
@@ -252,10 +265,11 @@ __global__ void __launch_bounds__(256) mg_extend(MgArgs A) {
         ok = u > v[0];
 #pragma unroll
         for (int q = 1; q < I; q++) ok = ok && u != v[q];
-        // first neighbour: u in no list of an earlier position
+        // first neighbour: u in no list of an earlier position (the lanes
+        // that search list q search it with the same trip count)
 #pragma unroll
         for (int q = 0; q < I - 1; q++)
-          if (q < j && ok) ok = !contains_dev(A.col + st[q], ln[q], u);
+          if (q < j && ok) ok = !member_u(A.col + st[q], ln[q], u);
         ok = ok && (j == I - 1 || fl < j || (fl == j && v[I - 1] < u));
       }
       if (MODE == mgCount) {
@@ -277,7 +291,7 @@ __global__ void __launch_bounds__(256) mg_extend(MgArgs A) {
           int code = code_in | (1 << pair_bit(j, I));
 #pragma unroll
           for (int q = 1; q < I; q++)
-            if (q > j && contains_dev(A.col + st[q], ln[q], u)) code |= 1 << pair_bit(q, I);
+            if (q > j && member_u(A.col + st[q], ln[q], u)) code |= 1 << pair_bit(q, I);
           cls = cls_of[code];
         }
         if (MODE == mgHist) {
