@@ -298,10 +298,11 @@ def test_bad_arguments_and_degenerate_graphs():
             with pytest.raises(pgm.PgmError) as e:
                 pgm.pgm_count_kcliques(h, k)
             assert e.value.status == pgm.PGM_EUNSUPPORTED
-        for k in (2, 5):
+        for k in (2, 6):
             with pytest.raises(pgm.PgmError) as e:
                 pgm.pgm_count_motifs(h, k)
             assert e.value.status == pgm.PGM_EUNSUPPORTED
+        assert pgm.pgm_count_motifs(h, 5) == [0] * 20 + [1]  # K5: one 5-clique (last class)
         with pytest.raises(pgm.PgmError):
             pgm.pgm_count_kcliques_range(h, 3, 3, 2)
         assert pgm.pgm_count_kcliques(h, 5) == 1 and pgm.pgm_count_kcliques(h, 1) == 5
@@ -311,6 +312,7 @@ def test_bad_arguments_and_degenerate_graphs():
     h = pgm.pgm_graph_create_csr(0, np.zeros(1, np.int64), np.zeros(0, np.int32))
     try:
         assert pgm.pgm_count_kcliques(h, 4) == 0 and pgm.pgm_count_motifs(h, 4) == [0] * 6
+        assert pgm.pgm_count_motifs(h, 5) == [0] * 21
     finally:
         pgm.pgm_graph_destroy(h)
 
