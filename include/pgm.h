@@ -220,6 +220,15 @@ pgm_status pgm_count_motifs_range(pgm_graph *g, int32_t k, int32_t v_lo, int32_t
  * Requires n < 2^30. */
 pgm_status pgm_list_motifs(pgm_graph *g, int32_t k, int32_t *out_dev, int64_t cap_rows, int64_t *n_rows);
 
+/* pgm_list_motifs with the rows written to a HOST buffer out_host
+ * (cap_rows * (k + 1) int32), for listings larger than device memory.  The
+ * last level is inspected (rows per entry), cut into entry ranges whose
+ * rows fit a device staging buffer of max(min(level_budget, 2^26),
+ * (k - 1) * d_max) rows, emitted there and copied out on a copy stream
+ * while the other of two staging buffers fills.  Rows are in chunk order;
+ * same size query, overflow and k rules as pgm_list_motifs. */
+pgm_status pgm_list_motifs_host(pgm_graph *g, int32_t k, int32_t *out_host, int64_t cap_rows, int64_t *n_rows);
+
 /* --------------------------------------------------------------- batches */
 
 /* A batch is the disjoint union of G graphs in one concatenated CSR: graph

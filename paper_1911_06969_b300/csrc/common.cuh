@@ -162,8 +162,10 @@ pgm_status graph_dag_arcs(Graph& g, int32_t v_lo, int32_t v_hi, int64_t* arcs);
 // 5-motif counts (21 classes) of the connected 5-sets whose minimum vertex is in [v_lo, v_hi)
 pgm_status count_motifs5(Graph& g, Workspace& ws, cudaStream_t s, int32_t v_lo, int32_t v_hi, uint64_t* out);
 // rows of k IDs (canonical order) + class of every connected k-set, k = 3..5, into out_dev
+struct HostSink;
+// (sink: rows streamed to host memory instead, out_dev unused)
 pgm_status list_motifs(Graph& g, Workspace& ws, cudaStream_t s, int k, int32_t* out_dev, int64_t cap_rows,
-                       int64_t* n_rows);
+                       int64_t* n_rows, HostSink* sink);
 // motif count on exactly this graph's IDs (count_motifs may switch to a relabelled copy)
 pgm_status count_motifs_on(Graph& g, Workspace& ws, cudaStream_t s, int k, int32_t v_lo, int32_t v_hi,
                            uint64_t* out, unsigned long long* per_graph_dev);
@@ -173,6 +175,74 @@ pgm_status graph_relabeled(Graph& g, int order, Graph** out);
 // out[i] = (int32) in[i] on the stream
 void narrow_rowptr(const int64_t* in, int32_t* out, int64_t len, cudaStream_t s);
 void graph_free(Graph& g);
+
+// Rows streamed to host memory: the last level of every edge-blocking chunk
+// is emitted into one of two device staging buffers; a full buffer is
+// copied to the host on a copy stream while the counting stream fills the
+// other.  Chunks are cut so that one chunk's rows fit a staging buffer;
+// device memory stays bounded by the staging size whatever the number of
+// rows.
+struct HostSink {
+  int32_t* host = nullptr;  // caller's rows
+  int64_t cap_rows = 0;     // rows per staging buffer
+  int64_t written = 0;      // rows already copied (or being copied) to the host
+  int64_t fill = 0;         // rows in the current staging buffer
+  int cur = 0;
+  int32_t* buf[2] = {nullptr, nullptr};
+  cudaStream_t copy = nullptr;
+  cudaEvent_t filled[2] = {nullptr, nullptr};  // on the counting stream: buffer's rows written
+  cudaEvent_t done[2] = {nullptr, nullptr};    // on the copy stream: buffer copied out
+  int k = 0;  // int32 per row
+
+  pgm_status init(int row_ints, int64_t rows) {
+    k = row_ints;
+    cap_rows = rows;
+    PGM_TRY_CUDA(cudaStreamCreateWithFlags(&copy, cudaStreamNonBlocking));
+    for (int b = 0; b < 2; b++) {
+      PGM_TRY_CUDA(cudaMalloc(&buf[b], (size_t)rows * k * sizeof(int32_t)));
+      PGM_TRY_CUDA(cudaEventCreateWithFlags(&filled[b], cudaEventDisableTiming));
+      PGM_TRY_CUDA(cudaEventCreateWithFlags(&done[b], cudaEventDisableTiming));
+    }
+    return PGM_OK;
+  }
+  // hand the current buffer to the copy stream; the counting stream then
+  // writes the other one once its previous copy has finished
+  pgm_status flush(cudaStream_t s) {
+    if (fill > 0) {
+      PGM_TRY_CUDA(cudaEventRecord(filled[cur], s));
+      PGM_TRY_CUDA(cudaStreamWaitEvent(copy, filled[cur], 0));
+      PGM_TRY_CUDA(cudaMemcpyAsync(host + written * k, buf[cur], (size_t)fill * k * sizeof(int32_t),
+                                   cudaMemcpyDeviceToHost, copy));
+      PGM_TRY_CUDA(cudaEventRecord(done[cur], copy));
+      written += fill;
+      fill = 0;
+      cur ^= 1;
+      PGM_TRY_CUDA(cudaStreamWaitEvent(s, done[cur], 0));  // no-op before the buffer's first copy
+    }
+    return PGM_OK;
+  }
+  pgm_status finish() {
+    if (copy) PGM_TRY_CUDA(cudaStreamSynchronize(copy));
+    return PGM_OK;
+  }
+  // staging space for n more rows (n <= cap_rows)
+  pgm_status reserve(int64_t n, cudaStream_t s) {
+    if (fill + n > cap_rows) PGM_TRY(flush(s));
+    return PGM_OK;
+  }
+  void release() {
+    if (copy) cudaStreamSynchronize(copy);
+    for (int b = 0; b < 2; b++) {
+      if (buf[b]) cudaFree(buf[b]);
+      if (filled[b]) cudaEventDestroy(filled[b]);
+      if (done[b]) cudaEventDestroy(done[b]);
+      buf[b] = nullptr;
+      filled[b] = done[b] = nullptr;
+    }
+    if (copy) cudaStreamDestroy(copy);
+    copy = nullptr;
+  }
+};
 
 // scan: out[i] = sum cnt[0..i), out[len] = total (device pointers)
 pgm_status exclusive_scan(const uint32_t* cnt, int64_t len, int64_t* out, Workspace& ws,

@@ -346,6 +346,8 @@ struct MgRun {
   int64_t budget;
   int32_t* rows_out = nullptr;  // listing: caller's row buffer
   int64_t rows_cap = 0;
+  HostSink* sink = nullptr;     // listing to host memory: staging buffers
+  int64_t host_rows = 0;
   double lvl_size[6] = {0, 0, 0, 0, 0, 0};
   int chunks = 0;
 
@@ -374,7 +376,7 @@ struct MgRun {
     switch (i) {
       case 2: return launch_t<MODE, 2>(A);
       case 3: return launch_t<MODE, 3>(A);
-      case 4: return launch_t<MODE == mgCount || MODE == mgWrite ? mgHist : MODE, 4>(A);  // never extended
+      case 4: return launch_t<MODE == mgWrite ? mgHist : MODE, 4>(A);  // never extended
     }
     set_error("motif engine: level %d", i);
     return PGM_EINVAL;
@@ -394,7 +396,8 @@ struct MgRun {
     A.tup = tup;
     A.p_lo = 0;
     A.p_hi = E;
-    if (i == k - 1) {
+    const bool last = i == k - 1;
+    if (last && !sink) {
       if (rows_out) {
         A.out = rows_out;
         A.out_E = rows_cap;
@@ -402,6 +405,7 @@ struct MgRun {
       }
       return launch<mgHist>(A, i);
     }
+    // inspection: children per entry (the rows themselves at the last level)
     PGM_TRY(ws.cnt[i].reserve((size_t)E));
     PGM_TRY(ws.off[i].reserve((size_t)E + 1));
     A.cnt = ws.cnt[i].p;
@@ -410,19 +414,20 @@ struct MgRun {
     int64_t T = 0;
     PGM_TRY(read_dev(ws.off[i].p + E, &T, s));
     if (T == 0) return PGM_OK;
+    const int64_t B = last ? std::min<int64_t>(budget, sink->cap_rows) : budget;
     // children of entries [pa, pb) fit the budget (at least one entry per chunk)
     int64_t pa = 0;
     while (pa < E) {
       int64_t base, pb = E;
       PGM_TRY(read_dev(ws.off[i].p + pa, &base, s));
-      if (T - base > budget) {
+      if (T - base > B) {
         int64_t lo = pa + 1, hi = E;
         pb = pa + 1;
         while (lo <= hi) {
           const int64_t mid = lo + (hi - lo) / 2;
           int64_t om;
           PGM_TRY(read_dev(ws.off[i].p + mid, &om, s));
-          if (om - base <= budget) {
+          if (om - base <= B) {
             pb = mid;
             lo = mid + 1;
           } else {
@@ -434,7 +439,22 @@ struct MgRun {
       PGM_TRY(read_dev(ws.off[i].p + pb, &ob, s));
       const int64_t Tp = ob - base;
       chunks++;
-      if (Tp > 0) {
+      if (Tp > 0 && last) {
+        // this chunk's rows into the current staging buffer
+        if (Tp > sink->cap_rows) {
+          set_error("list_motifs: %lld rows of one entry range exceed the staging buffer", (long long)Tp);
+          return PGM_ENOMEM;
+        }
+        PGM_TRY(sink->reserve(Tp, s));
+        PGM_TRY_CUDA(cudaMemsetAsync(ws.ctr.p + kRowsg, 0, sizeof(unsigned long long), s));
+        A.p_lo = pa;
+        A.p_hi = pb;
+        A.out = sink->buf[sink->cur] + sink->fill * (int64_t)(k + 1);
+        A.out_E = Tp;
+        PGM_TRY(launch<mgEmit>(A, i));
+        sink->fill += Tp;
+        host_rows += Tp;
+      } else if (Tp > 0) {
         PGM_TRY(ws.vid[i + 1].reserve((size_t)(i + 2) * (size_t)Tp));
         A.off = ws.off[i].p + pa;
         A.off_shift = base;
@@ -487,12 +507,18 @@ pgm_status count_motifs5(Graph& g, Workspace& ws, cudaStream_t s, int32_t v_lo, 
 }
 
 pgm_status list_motifs(Graph& g, Workspace& ws, cudaStream_t s, int k, int32_t* out_dev, int64_t cap_rows,
-                       int64_t* n_rows) {
+                       int64_t* n_rows, HostSink* sink) {
   MgRun run{g, ws, s, k, std::max<int64_t>(options().level_budget / 8, 1024)};
   run.rows_out = out_dev;
   run.rows_cap = cap_rows;
+  run.sink = sink;
   unsigned long long h[kSlotsg];
   PGM_TRY(run.run(0, g.n, h));
+  if (sink) {
+    PGM_TRY(sink->flush(s));
+    PGM_TRY(sink->finish());
+    h[kRowsg] = (unsigned long long)run.host_rows;
+  }
   *n_rows = (int64_t)h[kRowsg];
   if (h[kErrg] || (int64_t)h[kRowsg] > cap_rows) {
     set_error("list_motifs: %llu rows exceed the capacity of %lld", h[kRowsg], (long long)cap_rows);
@@ -506,13 +532,14 @@ pgm_status list_motifs(Graph& g, Workspace& ws, cudaStream_t s, int k, int32_t* 
 
 extern "C" {
 
-pgm_status pgm_list_motifs(pgm_graph* g, int32_t k, int32_t* out_dev, int64_t cap_rows, int64_t* n_rows) {
+static pgm_status list_motifs_to(pgm_graph* g, int32_t k, int32_t* out, int64_t cap_rows, int64_t* n_rows,
+                                  bool host, const char* name) {
   if (!g || !n_rows || cap_rows < 0) {
-    pgm::set_error("pgm_list_motifs: bad arguments");
+    pgm::set_error("%s: bad arguments", name);
     return PGM_EINVAL;
   }
   if (k < 3 || k > 5) {
-    pgm::set_error("pgm_list_motifs: k=%d unsupported (3, 4 or 5)", k);
+    pgm::set_error("%s: k=%d unsupported (3, 4 or 5)", name, k);
     return PGM_EUNSUPPORTED;
   }
   pgm::Graph& G = g->g;
@@ -522,26 +549,50 @@ pgm_status pgm_list_motifs(pgm_graph* g, int32_t k, int32_t* out_dev, int64_t ca
   uint64_t total = 0;
   for (int i = 0; i < 21; i++) total += c[i];
   if (total > (uint64_t)INT64_MAX / (uint64_t)(k + 1)) {
-    pgm::set_error("pgm_list_motifs: %llu rows do not fit an index", (unsigned long long)total);
+    pgm::set_error("%s: %llu rows do not fit an index", name, (unsigned long long)total);
     return PGM_EOVERFLOW;
   }
   *n_rows = (int64_t)total;
-  if (!out_dev) return PGM_OK;  // size query
+  if (!out) return PGM_OK;  // size query
   if ((int64_t)total > cap_rows) {
-    pgm::set_error("pgm_list_motifs: %llu rows exceed the capacity of %lld", (unsigned long long)total,
-                   (long long)cap_rows);
+    pgm::set_error("%s: %llu rows exceed the capacity of %lld", name, (unsigned long long)total, (long long)cap_rows);
     return PGM_EOVERFLOW;
   }
   if (total == 0) return PGM_OK;
-  pgm::profiler().start(G.stream);
   int64_t written = 0;
-  PGM_TRY(pgm::list_motifs(G, G.ws, G.stream, k, out_dev, (int64_t)total, &written));
+  pgm_status st = PGM_OK;
+  if (!host) {
+    pgm::profiler().start(G.stream);
+    st = pgm::list_motifs(G, G.ws, G.stream, k, out, (int64_t)total, &written, nullptr);
+  } else {
+    // staging rows: a chunk holds at least one entry, whose rows are at most
+    // the neighbours of its k - 1 vertices
+    pgm::HostSink sink;
+    sink.host = out;
+    const int64_t staging = std::max<int64_t>(std::min<int64_t>(pgm::options().level_budget, (int64_t)1 << 26),
+                                              (int64_t)(k - 1) * G.dmax);
+    st = sink.init(k + 1, staging);
+    if (st == PGM_OK) {
+      pgm::profiler().start(G.stream);
+      st = pgm::list_motifs(G, G.ws, G.stream, k, nullptr, (int64_t)total, &written, &sink);
+    }
+    cudaStreamSynchronize(G.stream);
+    sink.release();
+  }
+  PGM_TRY(st);
   if (written != (int64_t)total) {
-    pgm::set_error("pgm_list_motifs: %lld rows written, %llu counted", (long long)written,
-                   (unsigned long long)total);
+    pgm::set_error("%s: %lld rows written, %llu counted", name, (long long)written, (unsigned long long)total);
     return PGM_EINVAL;
   }
   return PGM_OK;
+}
+
+pgm_status pgm_list_motifs(pgm_graph* g, int32_t k, int32_t* out_dev, int64_t cap_rows, int64_t* n_rows) {
+  return list_motifs_to(g, k, out_dev, cap_rows, n_rows, false, "pgm_list_motifs");
+}
+
+pgm_status pgm_list_motifs_host(pgm_graph* g, int32_t k, int32_t* out_host, int64_t cap_rows, int64_t* n_rows) {
+  return list_motifs_to(g, k, out_host, cap_rows, n_rows, true, "pgm_list_motifs_host");
 }
 
 }  // extern "C"

@@ -99,6 +99,7 @@ _SIGS = {
     "pgm_list_kcliques": (C.c_int, [P, C.c_int32, P, C.c_int64, C.POINTER(C.c_int64)]),
     "pgm_list_motifs": (C.c_int, [P, C.c_int32, P, C.c_int64, C.POINTER(C.c_int64)]),
     "pgm_list_kcliques_host": (C.c_int, [P, C.c_int32, P, C.c_int64, C.POINTER(C.c_int64)]),
+    "pgm_list_motifs_host": (C.c_int, [P, C.c_int32, P, C.c_int64, C.POINTER(C.c_int64)]),
     "pgm_count_motifs": (C.c_int, [P, C.c_int32, P, C.c_int32]),
     "pgm_count_motifs_range": (C.c_int, [P, C.c_int32, C.c_int32, C.c_int32, P, C.c_int32]),
     "pgm_batch_create": (C.c_int, [C.c_int32, P, P, P, C.c_uint32, P, C.POINTER(P)]),
@@ -239,6 +240,21 @@ def pgm_list_motifs(g: int, k: int, out_dev_ptr: int = 0, cap_rows: int = 0) -> 
     connected k-sets (out_dev_ptr = 0: size query)."""
     n = C.c_int64()
     _ok(load().pgm_list_motifs(g, k, out_dev_ptr or None, cap_rows, C.byref(n)), "pgm_list_motifs")
+    return int(n.value)
+
+
+def pgm_list_motifs_host(g: int, k: int, out=None) -> int:
+    """Rows of k vertex IDs (canonical order) + pattern index into the host
+    array ``out`` (int32, shape (rows, k + 1), C-contiguous); returns the
+    number of connected k-sets (out = None: size query)."""
+    n = C.c_int64()
+    if out is None:
+        _ok(load().pgm_list_motifs_host(g, k, None, 0, C.byref(n)), "pgm_list_motifs_host")
+    else:
+        if out.dtype != np.int32 or not out.flags["C_CONTIGUOUS"] or (out.ndim == 2 and out.shape[1] != k + 1):
+            raise ValueError("out must be a C-contiguous int32 array of shape (rows, k + 1)")
+        _ok(load().pgm_list_motifs_host(g, k, out.ctypes.data, out.size // (k + 1), C.byref(n)),
+            "pgm_list_motifs_host")
     return int(n.value)
 
 

@@ -224,3 +224,28 @@ def test_list_motifs_chunked_and_overflow():
             assert e.value.status == pgm.PGM_EUNSUPPORTED
     finally:
         pgm.pgm_graph_destroy(h)
+
+
+def test_list_motifs_to_host():
+    """Motif rows streamed to host memory equal the device listing, also when
+    the last level is cut into many staging-sized chunks."""
+    g = gg.barabasi_albert(150, 2, seed=37)
+    defaults = pgm.pgm_get_options()
+    h = pgm.pgm_graph_create_csr(g.n, g.rowptr, g.col)
+    try:
+        for budget in (0, 1024):
+            if budget:
+                pgm.pgm_set_options(level_budget=budget)
+            for k in (3, 4, 5):
+                dev = list_motif_rows(g, k)
+                n = pgm.pgm_list_motifs_host(h, k)
+                out = np.full((n, k + 1), -1, np.int32)
+                assert pgm.pgm_list_motifs_host(h, k, out) == n == len(dev)
+                assert sorted(map(tuple, out)) == sorted(map(tuple, dev)), (budget, k)
+        small = np.zeros((n - 1, 6), np.int32)
+        with pytest.raises(pgm.PgmError) as e:
+            pgm.pgm_list_motifs_host(h, 5, small)
+        assert e.value.status == pgm.PGM_EOVERFLOW
+    finally:
+        pgm.pgm_set_options(**defaults)
+        pgm.pgm_graph_destroy(h)
