@@ -258,8 +258,8 @@ typedef struct {
 /* Per-graph motif counts of every graph of the batch in one pass of the
  * level engine over the union (persistent kernels pulling parents from a
  * device queue, counts attributed per graph), optionally replayed as a
- * captured CUDA graph.  out: host uint64[G * (k==3 ? 2 : 6)], row i =
- * graph i in pgm_count_motifs order.  t may be NULL (defaults). */
+ * captured CUDA graph.  k = 3, 4, 5; out: host uint64[G * (2, 6 or 21)],
+ * row i = graph i in pgm_count_motifs order.  t may be NULL (defaults). */
 pgm_status pgm_batch_count_motifs(pgm_batch *b, int32_t k, uint64_t *out, const pgm_tune *t);
 
 /* Per-graph k-clique counts (out: host uint64[G]). */

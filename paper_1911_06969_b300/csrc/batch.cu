@@ -65,7 +65,7 @@ struct pgm_batch {
   pgm::Graph g;
   int32_t G = 0;
   std::vector<int64_t> vtx_off;
-  pgm::DevArr<unsigned long long> per_graph;  // G * 6
+  pgm::DevArr<unsigned long long> per_graph;  // G * 21 (the largest pattern count, k = 5)
   unsigned long long* pinned_pg = nullptr;    // host-pinned copy of per_graph
   unsigned long long* pinned_ctr = nullptr;   // host-pinned counter block
   cudaStream_t own_stream = nullptr;          // created when the caller passes NULL
@@ -127,10 +127,10 @@ pgm_status check_tune(const pgm_tune* t) {
   return PGM_OK;
 }
 
-int npat(int kind, int k) { return kind == kClique ? 1 : (k == 3 ? 2 : 6); }
+int npat(int kind, int k) { return kind == kClique ? 1 : (k == 3 ? 2 : k == 4 ? 6 : 21); }
 
 pgm_status engine(pgm_batch* b, Workspace& ws, int kind, int k, unsigned long long* pg) {
-  uint64_t tmp[6];
+  uint64_t tmp[21];
   Graph& g = b->g;
   if (kind == kMotif) return count_motifs(g, ws, g.stream, k, 0, g.n, tmp, pg);
   return count_kcliques(g, ws, g.stream, k, 0, g.n, tmp, pg);
@@ -164,8 +164,8 @@ pgm_status run_batch(pgm_batch* b, int kind, int k, uint64_t* out, const pgm_tun
     }
     return PGM_OK;
   }
-  if (kind == kMotif && k != 3 && k != 4) {
-    set_error("batch: motif size k=%d unsupported (3 or 4)", k);
+  if (kind == kMotif && (k < 3 || k > 5)) {
+    set_error("batch: motif size k=%d unsupported (3, 4 or 5)", k);
     return PGM_EUNSUPPORTED;
   }
   if (kind == kClique && (k < 1 || k > 10)) {
@@ -349,9 +349,9 @@ pgm_status pgm_batch_create(int32_t G, const int64_t* vtx_off, const int64_t* ro
   st = pgm::graph_orient(b->g);
   if (st == PGM_OK) st = pgm::graph_prepare_motifs(b->g);
   if (st != PGM_OK) return fail(st);
-  st = b->per_graph.reserve((size_t)std::max(G, 1) * 6);
+  st = b->per_graph.reserve((size_t)std::max(G, 1) * 21);
   if (st != PGM_OK) return fail(st);
-  if (cudaMallocHost(&b->pinned_pg, (size_t)std::max(G, 1) * 6 * sizeof(unsigned long long)) != cudaSuccess ||
+  if (cudaMallocHost(&b->pinned_pg, (size_t)std::max(G, 1) * 21 * sizeof(unsigned long long)) != cudaSuccess ||
       cudaMallocHost(&b->pinned_ctr, 128 * sizeof(unsigned long long)) != cudaSuccess) {
     cudaGetLastError();
     pgm::set_error("pgm_batch_create: pinned host allocation failed");
@@ -382,11 +382,11 @@ pgm_status pgm_batch_count_motifs_loop(pgm_batch* b, int32_t k, uint64_t* out) {
     pgm::set_error("pgm_batch_count_motifs_loop: null argument");
     return PGM_EINVAL;
   }
-  if (k != 3 && k != 4) {
+  if (k < 3 || k > 5) {
     pgm::set_error("pgm_batch_count_motifs_loop: k=%d unsupported", k);
     return PGM_EUNSUPPORTED;
   }
-  const int np = k == 3 ? 2 : 6;
+  const int np = k == 3 ? 2 : k == 4 ? 6 : 21;
   // the same graph the batched pass counts on (the relabelled copy keeps
   // every graph's block of IDs), restricted to one graph's range per call
   // (no per-graph attribution; one plain engine call per graph)
@@ -401,7 +401,7 @@ pgm_status pgm_batch_count_motifs_loop(pgm_batch* b, int32_t k, uint64_t* out) {
   pgm_status st = PGM_OK;
   for (int32_t i = 0; i < b->G && st == PGM_OK; i++) {
     pgm::profiler().start(g.stream);
-    uint64_t c[6];
+    uint64_t c[21];
     st = pgm::count_motifs_on(g, b->g.ws, g.stream, k, (int32_t)b->vtx_off[i], (int32_t)b->vtx_off[i + 1], c,
                               nullptr);
     if (st == PGM_OK) memcpy(out + (int64_t)i * np, c, np * sizeof(uint64_t));

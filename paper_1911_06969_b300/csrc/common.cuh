@@ -160,7 +160,9 @@ pgm_status graph_host_dag_rp(Graph& g);
 // arcs of the DAG whose source lies in [v_lo, v_hi)
 pgm_status graph_dag_arcs(Graph& g, int32_t v_lo, int32_t v_hi, int64_t* arcs);
 // 5-motif counts (21 classes) of the connected 5-sets whose minimum vertex is in [v_lo, v_hi)
-pgm_status count_motifs5(Graph& g, Workspace& ws, cudaStream_t s, int32_t v_lo, int32_t v_hi, uint64_t* out);
+// (per_graph_dev: batches, 21 counts per graph added on the device instead)
+pgm_status count_motifs5(Graph& g, Workspace& ws, cudaStream_t s, int32_t v_lo, int32_t v_hi, uint64_t* out,
+                         unsigned long long* per_graph_dev);
 // rows of k IDs (canonical order) + class of every connected k-set, k = 3..5, into out_dev
 struct HostSink;
 // (sink: rows streamed to host memory instead, out_dev unused)

@@ -1013,10 +1013,6 @@ pgm_status count_motifs(Graph& g, Workspace& ws, cudaStream_t s, int k, int32_t 
     set_error("count_motifs: bad vertex range [%d, %d)", v_lo, v_hi);
     return PGM_EINVAL;
   }
-  if (k == 5 && per_graph_dev) {
-    set_error("count_motifs: k=5 has no per-graph (batch) attribution");
-    return PGM_EUNSUPPORTED;
-  }
   if (g.n >= (1 << 30)) {
     set_error("count_motifs: n=%d needs 30-bit vertex IDs", g.n);
     return PGM_EUNSUPPORTED;
@@ -1032,7 +1028,7 @@ pgm_status count_motifs(Graph& g, Workspace& ws, cudaStream_t s, int k, int32_t 
 
 pgm_status count_motifs_on(Graph& g, Workspace& ws, cudaStream_t s, int k, int32_t v_lo, int32_t v_hi,
                            uint64_t* out, unsigned long long* per_graph_dev) {
-  if (k == 5) return count_motifs5(g, ws, s, v_lo, v_hi, out);
+  if (k == 5) return count_motifs5(g, ws, s, v_lo, v_hi, out, per_graph_dev);
   MotifRun run(g, ws, s, k);
   run.per_graph = per_graph_dev;
   PGM_TRY(run.prepare());

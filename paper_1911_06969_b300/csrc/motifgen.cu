@@ -151,6 +151,8 @@ struct MgArgs {
   unsigned long long* rows;  // emit mode: rows written so far (row cursor)
   unsigned long long* err;   // emit mode: set when a row would pass the capacity
   unsigned long long* hist;  // hist mode: class counts
+  const int32_t* gid;        // batches: vertex -> graph (nullptr otherwise)
+  unsigned long long* per_graph;  // batches: 21 class counts per graph (hist mode)
   unsigned long long* queue;
   unsigned long long* stat;  // neighbour elements scanned
 };
@@ -295,9 +297,15 @@ __global__ void __launch_bounds__(256) mg_extend(MgArgs A) {
           cls = cls_of[code];
         }
         if (MODE == mgHist) {
-          // one shared-memory atomic per distinct class among the 32 candidates
+          // one atomic per distinct class among the 32 candidates (all of
+          // one entry, so of one graph of a batch)
           const unsigned same = __match_any_sync(kFull, cls);
-          if (cls >= 0 && lane == __ffs(same) - 1) atomicAdd(&hist[cls], (unsigned long long)__popc(same));
+          if (cls >= 0 && lane == __ffs(same) - 1) {
+            if (A.per_graph)
+              atomicAdd(A.per_graph + (int64_t)A.gid[v[0]] * kP5 + cls, (unsigned long long)__popc(same));
+            else
+              atomicAdd(&hist[cls], (unsigned long long)__popc(same));
+          }
         } else {
           const unsigned bal = __ballot_sync(kFull, ok);
           unsigned long long base = 0;
@@ -348,6 +356,7 @@ struct MgRun {
   int64_t rows_cap = 0;
   HostSink* sink = nullptr;     // listing to host memory: staging buffers
   int64_t host_rows = 0;
+  unsigned long long* per_graph = nullptr;  // batches: per-graph class counts
   double lvl_size[6] = {0, 0, 0, 0, 0, 0};
   int chunks = 0;
 
@@ -396,6 +405,8 @@ struct MgRun {
     A.tup = tup;
     A.p_lo = 0;
     A.p_hi = E;
+    A.gid = g.gid;
+    A.per_graph = per_graph;
     const bool last = i == k - 1;
     if (last && !sink) {
       if (rows_out) {
@@ -471,7 +482,8 @@ struct MgRun {
   }
 
   // the connected k-sets whose minimum vertex is in [v_lo, v_hi)
-  pgm_status run(int32_t v_lo, int32_t v_hi, unsigned long long* h) {
+  // (*deferred: replaying a recorded plan, the counters are read by the caller later)
+  pgm_status run(int32_t v_lo, int32_t v_hi, unsigned long long* h, bool* deferred) {
     if (g.n >= (1 << 30)) {
       set_error("motif engine: n=%d needs 30-bit vertex IDs", g.n);
       return PGM_EUNSUPPORTED;
@@ -482,8 +494,8 @@ struct MgRun {
     PGM_TRY_CUDA(cudaMemsetAsync(ws.ctr.p, 0, kSlotsg * sizeof(unsigned long long), s));
     const int64_t a_lo = g.h_rp[v_lo], a_hi = g.h_rp[v_hi];
     PGM_TRY(level(2, nullptr, a_hi - a_lo, a_lo));
-    bool deferred = false;
-    PGM_TRY(read_counters(ws.ctr.p, h, kSlotsg, s, &deferred));
+    PGM_TRY(read_counters(ws.ctr.p, h, kSlotsg, s, deferred));
+    if (*deferred) return PGM_OK;
     pgm_profile& lp = last_profile();
     Profiler& prof = profiler();
     if (prof.on) PGM_TRY(prof.finish(&lp));
@@ -496,10 +508,14 @@ struct MgRun {
 
 }  // namespace
 
-pgm_status count_motifs5(Graph& g, Workspace& ws, cudaStream_t s, int32_t v_lo, int32_t v_hi, uint64_t* out) {
+pgm_status count_motifs5(Graph& g, Workspace& ws, cudaStream_t s, int32_t v_lo, int32_t v_hi, uint64_t* out,
+                         unsigned long long* per_graph_dev) {
   MgRun run{g, ws, s, 5, std::max<int64_t>(options().level_budget / 8, 1024)};
+  run.per_graph = per_graph_dev;
   unsigned long long h[kSlotsg];
-  PGM_TRY(run.run(v_lo, v_hi, h));
+  bool deferred = false;
+  PGM_TRY(run.run(v_lo, v_hi, h, &deferred));
+  if (deferred) return PGM_OK;
   uint64_t t = 0;
   for (int c = 0; c < kP5; c++) t += out[c] = h[kHistg + c];
   last_profile().level_size[5] = t;
@@ -513,7 +529,8 @@ pgm_status list_motifs(Graph& g, Workspace& ws, cudaStream_t s, int k, int32_t* 
   run.rows_cap = cap_rows;
   run.sink = sink;
   unsigned long long h[kSlotsg];
-  PGM_TRY(run.run(0, g.n, h));
+  bool deferred = false;
+  PGM_TRY(run.run(0, g.n, h, &deferred));
   if (sink) {
     PGM_TRY(sink->flush(s));
     PGM_TRY(sink->finish());

@@ -290,8 +290,7 @@ def _tune_ptr(t):
 
 def pgm_batch_count_motifs(b: int, k: int, tune: pgm_tune | None = None) -> np.ndarray:
     G = load().pgm_batch_size(b)
-    npat = 2 if k == 3 else 6
-    out = np.zeros((max(G, 1), npat), np.uint64)
+    out = np.zeros((max(G, 1), max(_npat(k), 1)), np.uint64)
     _ok(load().pgm_batch_count_motifs(b, k, out.ctypes.data, _tune_ptr(tune)), "pgm_batch_count_motifs")
     return out[:G]
 
@@ -305,8 +304,7 @@ def pgm_batch_count_kcliques(b: int, k: int, tune: pgm_tune | None = None) -> np
 
 def pgm_batch_count_motifs_loop(b: int, k: int) -> np.ndarray:
     G = load().pgm_batch_size(b)
-    npat = 2 if k == 3 else 6
-    out = np.zeros((max(G, 1), npat), np.uint64)
+    out = np.zeros((max(G, 1), max(_npat(k), 1)), np.uint64)
     _ok(load().pgm_batch_count_motifs_loop(b, k, out.ctypes.data), "pgm_batch_count_motifs_loop")
     return out[:G]
 

@@ -83,3 +83,26 @@ def test_small_batch_20k_golden():
         assert hashlib.sha256(np.ascontiguousarray(got, np.uint64).tobytes()).hexdigest() == d["motif4_sha256"]
     finally:
         pgm.pgm_batch_destroy(h)
+
+
+def test_batch_motifs5():
+    """5-motif counts per graph of a batch (21 classes each): direct pass,
+    CUDA-graph replay and the per-graph loop all equal the oracle's."""
+    parts = [gg.empty(0), gg.complete(7), gg.star(12), gg.empty(2), gg.cycle(9), gg.path(8),
+             gg.complete_multipartite((3, 4, 4))]
+    parts += [gg.erdos_renyi(30 + 5 * i, 0.15, seed=80 + i) for i in range(6)]
+    parts += [gg.barabasi_albert(80 + 20 * i, 2 + i % 3, seed=90 + i) for i in range(6)]
+    b = gg.disjoint_union(parts)
+    want = np.array([oracle.esu_motifs(p, 5) for p in parts], dtype=np.uint64)
+    h = make_batch(b)
+    try:
+        assert np.array_equal(pgm.pgm_batch_count_motifs(h, 5), want)
+        assert np.array_equal(pgm.pgm_batch_count_motifs_loop(h, 5), want)
+        t = pgm.pgm_tune(256, 512, 512, 0, 1)
+        for _ in range(2):  # capture, then replay
+            assert np.array_equal(pgm.pgm_batch_count_motifs(h, 5, t), want)
+        with pytest.raises(pgm.PgmError) as e:
+            pgm.pgm_batch_count_motifs(h, 6)
+        assert e.value.status == pgm.PGM_EUNSUPPORTED
+    finally:
+        pgm.pgm_batch_destroy(h)
