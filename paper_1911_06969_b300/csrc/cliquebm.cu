@@ -206,9 +206,18 @@ __device__ __forceinline__ void bm_row_reverse(const int32_t* __restrict__ col, 
     }
     const int32_t kseg = __shfl_sync(kFull, key, seg);
     bool in = false;
-    if (j < d && kseg >= x) {
-      const int lo = seg * S;
-      in = contains_dev(col + b0 + lo, min(lo + S, dv) - lo, x);
+    const int lo = seg * S;
+    if (j < d && kseg >= x && lo < dv) {
+      // branch-free search of the segment: every lane's segment has S
+      // elements except the last, so the trip counts agree across the warp
+      const int32_t* a = col + b0 + lo;
+      int base = 0;
+      for (int n = min(lo + S, dv) - lo; n > 1;) {
+        const int half = n >> 1;
+        base = __ldg(a + base + half) <= x ? base + half : base;
+        n -= half;
+      }
+      in = __ldg(a + base) == x;
     }
     const unsigned bal = __ballot_sync(kFull, in);
     if (lane == 0 && bal) row[j0 >> 5] |= bal;
