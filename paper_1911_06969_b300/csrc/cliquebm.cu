@@ -226,7 +226,7 @@ __device__ __forceinline__ void bm_row_reverse(const int32_t* __restrict__ col, 
 
 // ----------------------------------------------------------- warp kernel
 // One vertex per warp, d <= 64: P and the rows (2 words, stride 2) in shared memory.
-__global__ void __launch_bounds__(256, 6) bm_warp_kernel(BmArgs B) {
+__global__ void __launch_bounds__(256, 8) bm_warp_kernel(BmArgs B) {
   __shared__ int32_t sP[8][kBmWarpD];
   __shared__ int32_t sB0[8][kBmWarpD];
   __shared__ int32_t sDv[8][kBmWarpD];
@@ -414,7 +414,7 @@ __host__ __device__ constexpr size_t bm_block_smem(int dmax, int threads) {
 
 // resident blocks per SM that the register budget is sized for
 __host__ __device__ constexpr int bm_min_blocks(int dmax, int threads) {
-  return dmax == 0 ? 2 : (threads <= 256 ? 6 : (threads <= 512 ? 3 : 1));
+  return dmax == 0 ? 2 : (threads <= 256 ? 8 : (threads <= 512 ? 3 : 1));
 }
 
 // FIVE selects the 5-clique variant (k = 5); the other handles k = 3 and 4.
