@@ -77,7 +77,7 @@ typedef struct {
   int32_t profile;         /* 1 = record per-launch CUDA-event times (pgm_last_profile)       */
   int32_t reverse_ratio;   /* intersect in reverse (scan the shorter list, search the longer)
                               when the longer is this many times longer (default 2)          */
-  int32_t clique_engine;   /* 0 = auto (bitset levels for k = 3..5; level lists otherwise),
+  int32_t clique_engine;   /* 0 = auto (bitset levels for k = 3..10, level lists if they do not fit),
                               1 = level lists (vid arrays + inspection-execution),
                               2 = bitset levels where supported                               */
   int32_t bitset_forward_ratio;  /* bitset rows: build row i by scanning N+(P[i]) when it is at most
@@ -147,10 +147,13 @@ void pgm_graph_destroy(pgm_graph *g);
  * k-vertex subsets whose vertices are pairwise adjacent.  k = 1 gives n,
  * k = 2 gives m; k in [3, 10] runs the level-wise engine on the oriented
  * DAG: extension of the last vertex only (eager pruning, Sec. 4.1), a
- * connectivity check of each candidate against the embedding by sorted
- * intersection with the parent's candidate list, inspection-execution
- * between materialised levels (Sec. 5.3), edge blocking (Sec. 5.2), and a
- * fused count at the last level (Sec. 3.1, reduce only at the last level).
+ * connectivity check of each candidate against the embedding, and a fused
+ * count at the last level (Sec. 3.1, reduce only at the last level).  The
+ * default engine keeps the level-3 children of each vertex as bit rows
+ * over its out-list, so deeper levels are ANDs of rows (k >= 6 walks the
+ * chains depth-first); the level-list engine (options.clique_engine = 1)
+ * materialises the levels with inspection-execution (Sec. 5.3), sorted
+ * intersection and edge blocking (Sec. 5.2).
  * Orients the graph first if needed.  Returns PGM_EUNSUPPORTED outside
  * [1, 10]. */
 pgm_status pgm_count_kcliques(pgm_graph *g, int32_t k, uint64_t *out_count);

@@ -425,8 +425,8 @@ pgm_status count_kcliques(Graph& g, Workspace& ws, cudaStream_t s, int k, int32_
     return PGM_OK;
   }
   const int engine = options().clique_engine;
-  if ((engine == 0 || engine == 2) && k >= 3 && k <= 5) {
-    uint64_t ls[3] = {0, 0, 0};
+  if ((engine == 0 || engine == 2) && k >= 3) {
+    uint64_t ls[kBmLevelRead + 1] = {0};
     const pgm_status st = count_kcliques_bitset(g, ws, s, k, v_lo, v_hi, out, per_graph_dev, ls);
     if (st != PGM_EUNSUPPORTED) {
       if (st != PGM_OK || current_plan()) return st;
@@ -437,13 +437,12 @@ pgm_status count_kcliques(Graph& g, Workspace& ws, cudaStream_t s, int k, int32_
           pgm_phase& p = lp.phase[i];
           // out-lists of the vertex and of each out-neighbour (4 B per element) + row pointers
           if (!strcmp(p.name, "bitset_count"))
-            p.alg_bytes = 4.0 * (double)ls[2] + 4.0 * p.entries + 8.0 * (double)(v_hi - v_lo);
+            p.alg_bytes = 4.0 * (double)ls[kBmLevelRead] + 4.0 * p.entries + 8.0 * (double)(v_hi - v_lo);
         }
       }
       lp.level_size[1] = (uint64_t)(v_hi - v_lo);
       lp.level_size[2] = (uint64_t)arcs;
-      if (k >= 4) lp.level_size[3] = ls[0];
-      if (k == 5) lp.level_size[4] = ls[1];
+      for (int l = 3; l < k; l++) lp.level_size[l] = ls[l];
       lp.level_size[k] = *out;
       lp.chunks = 0;
       return PGM_OK;

@@ -1,4 +1,4 @@
-// cliquebm.cu -- k-clique counting (k = 3, 4, 5) with bitset level lists.
+// cliquebm.cu -- k-clique counting (k = 3 .. 10) with bitset level lists.
 //
 // Same method as clique.cu (Sec. 3.3 Listing 3, Sec. 4.1): embeddings grow
 // by the last vertex only, and a candidate is kept iff it is connected to
@@ -12,6 +12,9 @@
 //   triangles at u  = sum_i popc(R_i)
 //   4-cliques at u  = sum_i sum_{j in R_i} popc(R_i & R_j)
 //   5-cliques at u  = sum_i sum_{j in R_i} sum_{l in R_i & R_j} popc(R_i & R_j & R_l)
+// and for k >= 6 a depth-first walk over chains j_1 in C_0 = R_i, j_2 in C_1,
+// ... with C_t = C_{t-1} & R_{j_t} (the level-(t+3) children of the chain),
+// whose leaves at depth k - 4 sum popc(C & R_l) over l in C.
 // Each clique is counted once, at its first vertex in DAG order.
 //
 // Rows are built per vertex by intersecting N+(P[i]) with P, forward (scan
@@ -32,8 +35,10 @@ constexpr int kBmWarpD = 64;     // warp kernel: d <= 64 (two words per row)
 constexpr int kBmGrab = 8;
 
 // counter slots: [0] warp queue, [kQPop + b] / [kQPush + b] pop / push
-// counters of bucket b, [8..10] counts, [12] statistics, [15] error
-constexpr int kQPop = 1, kQPush = 16, kBmBuckets = 4, kBmSlots = 20;
+// counters of bucket b, [8..10] counts, [12] statistics, [15] error,
+// [kDeepLvl + t] entries of level t + 3 for t = 2 .. kDeepMax (k >= 6)
+constexpr int kQPop = 1, kQPush = 16, kBmBuckets = 4, kDeepLvl = 20, kBmSlots = 28;
+constexpr int kDeepMax = 6;  // depth of the walk for k = 10
 
 struct BmArgs {
   const int32_t* rp;   // DAG
@@ -53,6 +58,8 @@ struct BmArgs {
   unsigned long long* stat;   // adjacency elements read while building rows
   const int32_t* gid;
   unsigned long long* per_graph;
+  unsigned long long* deep;   // k >= 6: [t] entries of level t + 3 (t = 2 .. k - 4)
+  int clevels;                // C buffers per warp: 1, or k - 4 for k >= 6
 };
 
 // bucket of a vertex with out-degree d > kBmWarpD
@@ -224,9 +231,53 @@ __device__ __forceinline__ void bm_row_reverse(const int32_t* __restrict__ col, 
   }
 }
 
+// k >= 6 in the warp kernel: the lane that owns row i walks the chains
+// below C_T = (c0, c1) (two words); at depth D it adds popc(C_D & R_l) for
+// every l in C_D.  lvl[t] counts the entries of level t + 3.
+template <int T>
+__device__ __forceinline__ void bm_deep_lane(uint32_t c0, uint32_t c1, const uint32_t* R, int D,
+                                             unsigned long long& leaf, unsigned long long (&lvl)[kDeepMax + 1]) {
+  if (T == D) {
+    for (int h = 0; h < 2; h++) {
+      uint32_t bits = h ? c1 : c0;
+      while (bits) {
+        const int l = (h << 5) + __ffs(bits) - 1;
+        bits &= bits - 1;
+        leaf += (unsigned long long)(__popc(c0 & R[2 * l]) + __popc(c1 & R[2 * l + 1]));
+      }
+    }
+    return;
+  }
+  if constexpr (T < kDeepMax) {
+    for (int h = 0; h < 2; h++) {
+      uint32_t bits = h ? c1 : c0;
+      while (bits) {
+        const int j = (h << 5) + __ffs(bits) - 1;
+        bits &= bits - 1;
+        const uint32_t n0 = c0 & R[2 * j], n1 = c1 & R[2 * j + 1];
+        const unsigned pc = (unsigned)(__popc(n0) + __popc(n1));
+        lvl[T + 1] += pc;
+        if (pc) bm_deep_lane<T + 1>(n0, n1, R, D, leaf, lvl);
+      }
+    }
+  }
+}
+
+// per-lane level counters of the walk -> the counter block (levels 5 ..)
+__device__ __forceinline__ void bm_deep_flush(const BmArgs& B, unsigned long long (&lvl)[kDeepMax + 1]) {
+#pragma unroll
+  for (int t = 2; t <= kDeepMax; t++) {
+    const unsigned long long x = warp_sum(lvl[t]);
+    if ((threadIdx.x & 31) == 0 && x) atomicAdd(B.deep + t, x);
+    lvl[t] = 0;
+  }
+}
+
 // ----------------------------------------------------------- warp kernel
 // One vertex per warp, d <= 64: P and the rows (2 words, stride 2) in shared memory.
-__global__ void __launch_bounds__(256, 8) bm_warp_kernel(BmArgs B) {
+// DEEP: k >= 6 (the walk); otherwise k = 3, 4, 5.
+template <bool DEEP>
+__global__ void __launch_bounds__(256, DEEP ? 4 : 8) bm_warp_kernel(BmArgs B) {
   __shared__ int32_t sP[8][kBmWarpD];
   __shared__ int32_t sB0[8][kBmWarpD];
   __shared__ int32_t sDv[8][kBmWarpD];
@@ -239,6 +290,7 @@ __global__ void __launch_bounds__(256, 8) bm_warp_kernel(BmArgs B) {
   int32_t* P = sP[wid];
   uint32_t* R = sR[wid];
   unsigned long long c[3] = {0, 0, 0};
+  unsigned long long lvl[kDeepMax + 1] = {0, 0, 0, 0, 0, 0, 0};
   unsigned long long seen = 0;
   int cur_g = -1;
   const int64_t np = (int64_t)B.v_hi - B.v_lo;
@@ -304,6 +356,10 @@ __global__ void __launch_bounds__(256, 8) bm_warp_kernel(BmArgs B) {
           continue;
         }
         c[1] += tri;
+        if constexpr (DEEP) {
+          bm_deep_lane<0>(r0, r1, R, B.k - 4, c[0], lvl);
+          continue;
+        }
         unsigned long long k4 = 0, k5 = 0;
         for (int h = 0; h < 2; h++) {
           uint32_t bits = h ? r1 : r0;
@@ -335,6 +391,12 @@ __global__ void __launch_bounds__(256, 8) bm_warp_kernel(BmArgs B) {
     }
   }
   bm_flush(B, c, cur_g, lane);
+  if constexpr (DEEP) {
+    // level 4 = lvl[1]; levels 5 .. k - 1 = lvl[2 ..]
+    const unsigned long long x = warp_sum(lvl[1]);
+    if (lane == 0 && x) atomicAdd(B.acc + 2, x);
+    bm_deep_flush(B, lvl);
+  }
   seen = warp_sum(seen);
   if (lane == 0 && seen) atomicAdd(B.stat, seen);
 }
@@ -400,26 +462,80 @@ __device__ __forceinline__ unsigned bm_and_popc4(const uint4* X, const uint4* Y,
   return s;
 }
 
-// Shared-memory bytes of bm_block_kernel<DMAX, THREADS>.
-__host__ __device__ constexpr size_t bm_block_smem(int dmax, int threads) {
+// Shared-memory bytes of bm_block_kernel<DMAX, THREADS, KV> with `clevels`
+// C buffers per warp (1, or k - 4 for the walk of k >= 6).
+__host__ __device__ constexpr size_t bm_block_smem(int dmax, int threads, int clevels) {
   return dmax > 0 ? (size_t)4 * dmax                       // P
                         + (size_t)8 * dmax                  // start and length of each out-list
                         + (size_t)4 * dmax                  // filter (up to dmax words)
                         + (size_t)(4 + 2) * 2 * dmax        // position table: 2 dmax keys + positions
                         + (size_t)4 * (threads / 32) * 128  // two 64-entry buffers per warp
-                        + (size_t)16 * (threads / 32) * bm_s4(dmax / 32)  // C = R_i & R_j per warp
-                        + (size_t)16 * dmax * bm_s4(dmax / 32)            // rows
+                        + (size_t)16 * (threads / 32) * bm_s4(dmax / 32) * clevels  // C buffers per warp
+                        + (size_t)16 * dmax * bm_s4(dmax / 32)                      // rows
                   : (size_t)4 * (threads / 32) * 128 + (size_t)4 * kBmGlobalFW;
 }
 
-// resident blocks per SM that the register budget is sized for
-__host__ __device__ constexpr int bm_min_blocks(int dmax, int threads) {
-  return dmax == 0 ? 2 : (threads <= 256 ? 8 : (threads <= 512 ? 3 : 1));
+// resident blocks per SM that the register budget is sized for (the walk
+// of k >= 6 keeps its level counters in registers: fewer, larger threads)
+__host__ __device__ constexpr int bm_min_blocks(int dmax, int threads, int kv) {
+  return kv == 6 ? (threads <= 256 ? 4 : (threads <= 512 ? 2 : 1))
+                 : (dmax == 0 ? 2 : (threads <= 256 ? 8 : (threads <= 512 ? 3 : 1)));
 }
 
-// FIVE selects the 5-clique variant (k = 5); the other handles k = 3 and 4.
-template <int DMAX, int THREADS, bool FIVE>
-__global__ void __launch_bounds__(THREADS, bm_min_blocks(DMAX, THREADS)) bm_block_kernel(BmArgs B, int bucket) {
+// k >= 6 in the block kernels: one warp walks the chains below C_T (W
+// words at Ct, 16-byte chunks n4), one j at a time: C_{T+1} = C_T & R_j goes
+// to buffer T of the warp (cstride words apart); at depth D the leaf adds
+// |C_D & R_l| for every l in C_D, one l per lane.  lvl[t] counts the
+// entries of level t + 3.
+template <int T, class RowFn>
+__device__ __forceinline__ void bm_deep_walk(const uint32_t* Ct, int D, int W, int n4, uint32_t* Cbuf,
+                                             int64_t cstride, const RowFn& row4, int* buf, int lane,
+                                             unsigned long long& leaf, unsigned long long (&lvl)[kDeepMax + 1]) {
+  if (T == D) {
+    int cnt = 0;
+    auto fl = [&](int l, bool valid) {
+      if (valid) leaf += bm_and_popc4(reinterpret_cast<const uint4*>(Ct), row4(l), n4);
+    };
+    for (int w0 = 0; w0 < W; w0 += 32) {
+      const uint32_t mine = w0 + lane < W ? Ct[w0 + lane] : 0u;
+      bm_bits(mine, w0, buf, cnt, lane, fl);
+    }
+    bm_bits_tail(buf, cnt, lane, fl);
+    return;
+  }
+  if constexpr (T < kDeepMax) {
+    uint32_t* Cn = Cbuf + (int64_t)T * cstride;  // C_{T+1}
+    for (int w0 = 0; w0 < W; w0 += 32) {
+      const uint32_t mine = w0 + lane < W ? Ct[w0 + lane] : 0u;
+      unsigned nz = __ballot_sync(kFull, mine != 0u);
+      while (nz) {
+        const int q = __ffs(nz) - 1;
+        nz &= nz - 1;
+        uint32_t word = __shfl_sync(kFull, mine, q);
+        while (word) {
+          const int j = ((w0 + q) << 5) + __ffs(word) - 1;
+          word &= word - 1;
+          const uint32_t* Rj = reinterpret_cast<const uint32_t*>(row4(j));
+          __syncwarp();  // the previous chain's readers of Cn are done
+          unsigned cn = 0;
+          for (int w = lane; w < 4 * n4; w += 32) {
+            const uint32_t x = Ct[w] & Rj[w];  // padding words are zero
+            Cn[w] = x;
+            cn += __popc(x);
+          }
+          lvl[T + 1] += cn;
+          __syncwarp();
+          if (__any_sync(kFull, cn != 0u))
+            bm_deep_walk<T + 1>(Cn, D, W, n4, Cbuf, cstride, row4, buf, lane, leaf, lvl);
+        }
+      }
+    }
+  }
+}
+
+// KV: 4 (k = 3, 4), 5 (k = 5) or 6 (k = 6 .. 10, the walk).
+template <int DMAX, int THREADS, int KV>
+__global__ void __launch_bounds__(THREADS, bm_min_blocks(DMAX, THREADS, KV)) bm_block_kernel(BmArgs B, int bucket) {
   constexpr int NW = THREADS / 32;
   constexpr int S4MAX = DMAX > 0 ? bm_s4(DMAX / 32) : 0;
   extern __shared__ __align__(16) uint32_t smem_u[];
@@ -436,10 +552,12 @@ __global__ void __launch_bounds__(THREADS, bm_min_blocks(DMAX, THREADS)) bm_bloc
   uint16_t* sPos = reinterpret_cast<uint16_t*>(smem_u + 6 * DMAX);
   int* buf = reinterpret_cast<int*>(smem_u) + kHead + wid * 128;
   int* buf2 = buf + 64;
-  uint32_t* sC = smem_u + kHead + NW * 128 + wid * 4 * S4MAX;
-  uint32_t* sRows = smem_u + kHead + NW * 128 + NW * 4 * S4MAX;
+  const int CL = KV == 6 ? B.clevels : 1;  // C buffers per warp
+  uint32_t* sC = smem_u + kHead + NW * 128 + wid * 4 * S4MAX * CL;
+  uint32_t* sRows = smem_u + kHead + NW * 128 + NW * 4 * S4MAX * CL;
   uint32_t* gRows = B.scratch ? B.scratch + (int64_t)blockIdx.x * B.scratch_words : nullptr;
   unsigned long long c[3] = {0, 0, 0};
+  unsigned long long lvl[kDeepMax + 1] = {0, 0, 0, 0, 0, 0, 0};
   unsigned long long seen = 0;
   int cur_g = -1;
   const long long nbig = min((long long)B.queue[kQPush + bucket], (long long)B.big_cap[bucket]);
@@ -531,7 +649,9 @@ __global__ void __launch_bounds__(THREADS, bm_min_blocks(DMAX, THREADS)) bm_bloc
     }
     __syncthreads();
     // level 3 and beyond: one warp per row i
-    uint32_t* C = DMAX > 0 ? sC : gRows + (int64_t)d * S + (int64_t)wid * S;  // R_i & R_j (5-cliques)
+    // C buffers of the warp: R_i & R_j (5-cliques) or the chain's C_1 .. C_D (k >= 6)
+    uint32_t* C = DMAX > 0 ? sC : gRows + (int64_t)d * S + (int64_t)wid * S * CL;
+    const int64_t cstride = DMAX > 0 ? 4 * S4MAX : S;
     // row j (32-bit offsets when the rows are in shared memory)
     auto row4 = [&](int j) {
       return reinterpret_cast<const uint4*>(DMAX > 0 ? R + j * S : R + (int64_t)j * S);
@@ -547,7 +667,9 @@ __global__ void __launch_bounds__(THREADS, bm_min_blocks(DMAX, THREADS)) bm_bloc
       }
       c[1] += tri;
       int cnt = 0;
-      if constexpr (!FIVE) {
+      if constexpr (KV == 6) {
+        bm_deep_walk<0>(Ri, B.k - 4, W, n4, C, cstride, row4, buf, lane, c[0], lvl);
+      } else if constexpr (KV == 4) {
         // 4-cliques: |R_i & R_j| for every j in R_i, one j per lane
         auto f4 = [&](int j, bool valid) {
           if (valid) c[0] += bm_and_popc4(Ri4, row4(j), n4);
@@ -595,20 +717,25 @@ __global__ void __launch_bounds__(THREADS, bm_min_blocks(DMAX, THREADS)) bm_bloc
     __syncthreads();
   }
   bm_flush(B, c, cur_g, lane);
+  if constexpr (KV == 6) {
+    const unsigned long long x = warp_sum(lvl[1]);  // level 4
+    if (lane == 0 && x) atomicAdd(B.acc + 2, x);
+    bm_deep_flush(B, lvl);
+  }
   seen = warp_sum(seen);
   if (lane == 0 && seen) atomicAdd(B.stat, seen);
 }
 
 }  // namespace
 
-// Bitset engine entry: counts k-cliques (k in 3..5) rooted in [v_lo, v_hi).
+// Bitset engine entry: counts k-cliques (k in 3..10) rooted in [v_lo, v_hi).
 // Returns PGM_EUNSUPPORTED when the DAG's largest out-degree would need more
 // than `max_scratch` bytes of row scratch (the caller then uses the
 // level-list engine).
 pgm_status count_kcliques_bitset(Graph& g, Workspace& ws, cudaStream_t s, int k, int32_t v_lo,
                                  int32_t v_hi, uint64_t* out, unsigned long long* per_graph_dev,
                                  uint64_t* level_sizes) {
-  if (k < 3 || k > 5) return PGM_EUNSUPPORTED;
+  if (k < 3 || k > 4 + kDeepMax) return PGM_EUNSUPPORTED;
   const pgm_options o = options();
   const int smem_d = o.bitset_smem_degree;
   const int64_t dmax = g.dag_dmax;
@@ -621,24 +748,31 @@ pgm_status count_kcliques_bitset(Graph& g, Workspace& ws, cudaStream_t s, int k,
     size_t smem;
     int grid;
   };
-  const bool five = k == 5;
+  const int kv = k <= 4 ? 4 : (k == 5 ? 5 : 6);
+  const int clevels = kv == 6 ? k - 4 : 1;
+  auto pick = [kv](const void* f4, const void* f5, const void* f6) { return kv == 4 ? f4 : (kv == 5 ? f5 : f6); };
   Kern kern[kBmBuckets] = {
-      {five ? (const void*)bm_block_kernel<256, 256, true> : (const void*)bm_block_kernel<256, 256, false>, 256,
-       bm_block_smem(256, 256), 0},
-      {five ? (const void*)bm_block_kernel<512, 512, true> : (const void*)bm_block_kernel<512, 512, false>, 512,
-       bm_block_smem(512, 512), 0},
-      {five ? (const void*)bm_block_kernel<1024, 1024, true> : (const void*)bm_block_kernel<1024, 1024, false>,
-       1024, bm_block_smem(1024, 1024), 0},
-      {five ? (const void*)bm_block_kernel<0, 512, true> : (const void*)bm_block_kernel<0, 512, false>, 512,
-       bm_block_smem(0, 512), 0},
+      {pick((const void*)bm_block_kernel<256, 256, 4>, (const void*)bm_block_kernel<256, 256, 5>,
+            (const void*)bm_block_kernel<256, 256, 6>),
+       256, bm_block_smem(256, 256, clevels), 0},
+      {pick((const void*)bm_block_kernel<512, 512, 4>, (const void*)bm_block_kernel<512, 512, 5>,
+            (const void*)bm_block_kernel<512, 512, 6>),
+       512, bm_block_smem(512, 512, clevels), 0},
+      {pick((const void*)bm_block_kernel<1024, 1024, 4>, (const void*)bm_block_kernel<1024, 1024, 5>,
+            (const void*)bm_block_kernel<1024, 1024, 6>),
+       1024, bm_block_smem(1024, 1024, clevels), 0},
+      {pick((const void*)bm_block_kernel<0, 512, 4>, (const void*)bm_block_kernel<0, 512, 5>,
+            (const void*)bm_block_kernel<0, 512, 6>),
+       512, bm_block_smem(0, 512, clevels), 0},
   };
+  const void* warp_fn = kv == 6 ? (const void*)bm_warp_kernel<true> : (const void*)bm_warp_kernel<false>;
 
   for (int b = 0; b < kBmBuckets; b++) {
     PGM_TRY(smem_attr(kern[b].fn, (int)kern[b].smem));
     kern[b].grid = grid_for(kern[b].fn, kern[b].threads, kern[b].smem);
   }
   // global-row bucket: d rows plus 16 warps' C buffers per block, 4 * S4 words each
-  const int64_t words = dmax > smem_d ? (dmax + 16) * 4 * (int64_t)bm_s4((int)Wmax) : 0;
+  const int64_t words = dmax > smem_d ? (dmax + 16 * (int64_t)clevels) * 4 * (int64_t)bm_s4((int)Wmax) : 0;
   if (words > 0 && (double)kern[3].grid * (double)words * 4.0 > 8.0 * (double)(1ull << 30)) {
     set_error("bitset engine: out-degree %lld needs too much row scratch", (long long)dmax);
     return PGM_EUNSUPPORTED;
@@ -676,12 +810,15 @@ pgm_status count_kcliques_bitset(Graph& g, Workspace& ws, cudaStream_t s, int k,
   B.stat = ws.ctr.p + 12;
   B.gid = g.gid;
   B.per_graph = per_graph_dev;
-  int wgrid = grid_for((const void*)bm_warp_kernel, 256, 0);
+  B.deep = ws.ctr.p + kDeepLvl;
+  B.clevels = clevels;
+  int wgrid = grid_for(warp_fn, 256, 0);
   wgrid = (int)std::max<int64_t>(1, std::min<int64_t>(wgrid, ((nv + kBmGrab - 1) / kBmGrab + 7) / 8));
   Profiler& prof = profiler();
   int id = prof.begin("bitset_count", 3);
   if (nv > 0) {
-    bm_warp_kernel<<<wgrid, 256, 0, s>>>(B);
+    void* wargv[] = {&B};
+    PGM_TRY_CUDA(cudaLaunchKernel(warp_fn, dim3(wgrid), dim3(256), wargv, 0, s));
     PGM_CHECK_LAUNCH();
     // largest rows first, so that the short tail of each launch is cheap
     for (int b = kBmBuckets - 1; b >= 0; b--) {
@@ -703,10 +840,11 @@ pgm_status count_kcliques_bitset(Graph& g, Workspace& ws, cudaStream_t s, int k,
     return PGM_ENOMEM;
   }
   *out = h[8];
-  if (level_sizes) {
-    level_sizes[0] = h[9];   // level 3 (triangles) for k >= 4
-    level_sizes[1] = h[10];  // level 4 (4-cliques) for k = 5
-    level_sizes[2] = h[12];  // adjacency elements read
+  if (level_sizes) {  // [l] entries of level l (3 <= l < k), [kBmLevelRead] adjacency elements read
+    level_sizes[3] = h[9];
+    level_sizes[4] = h[10];
+    for (int l = 5; l < k; l++) level_sizes[l] = h[kDeepLvl + (l - 3)];
+    level_sizes[kBmLevelRead] = h[12];
   }
   return PGM_OK;
 }

@@ -292,6 +292,9 @@ pgm_status read_counters(const unsigned long long* dev, unsigned long long* host
 // counting engines (results written on PGM_OK; per_graph_dev: batches)
 pgm_status count_kcliques(Graph& g, Workspace& ws, cudaStream_t s, int k, int32_t v_lo,
                           int32_t v_hi, uint64_t* out, unsigned long long* per_graph_dev);
+// bitset engine: level_sizes[l] = entries of level l (3 <= l < k),
+// level_sizes[kBmLevelRead] = adjacency elements read (array of kBmLevelRead + 1)
+constexpr int kBmLevelRead = 11;
 pgm_status count_kcliques_bitset(Graph& g, Workspace& ws, cudaStream_t s, int k, int32_t v_lo,
                                  int32_t v_hi, uint64_t* out, unsigned long long* per_graph_dev,
                                  uint64_t* level_sizes);

@@ -78,12 +78,13 @@ int64_t predict_bytes(const pgm_server* s, const SGraph& sg, const pgm_query& q)
   const int k = q.kind == PGM_Q_TRIANGLE ? 3 : q.k;
   double b = 8.0 * n + 4096.0;
   const int engine = pgm::options().clique_engine;
-  if (clique && k <= 5 && engine != 1) {
-    // bitset levels: bucket lists, plus row scratch when out-lists exceed the shared-memory rows
-    const double dm = (double)g.dag_dmax;
+  if (clique && engine != 1) {
+    // bitset levels: bucket lists, plus row scratch (rows and the warps' C
+    // buffers, k - 4 of them for k >= 6) when out-lists exceed the shared-memory rows
+    const double dm = (double)g.dag_dmax, cl = k >= 6 ? (double)(k - 4) : 1.0;
     b += 4.0 * n;
     if (g.dag_dmax > pgm::options().bitset_smem_degree)
-      b += 2.0 * pgm::num_sms() * (dm + 16.0) * (std::ceil(dm / 128.0) + 1.0) * 16.0;
+      b += 2.0 * pgm::num_sms() * (dm + 16.0 * cl) * (std::ceil(dm / 128.0) + 1.0) * 16.0;
   } else if (clique && k >= 4) {
     b += 12.0 * (arcs / 2) + 16.0 * std::min(sg.c2_dag, budget_entries);
     if (k >= 5) b += 16.0 * budget_entries;  // deeper levels: at most one budget chunk each

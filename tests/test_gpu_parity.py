@@ -350,3 +350,59 @@ def test_chung_lu_1m_motifs_golden():
     with pgm.Graph(g) as G:
         assert G.motifs(3) == d["motif3"]
         assert G.motifs(4) == d["motif4"]
+
+
+def _join_independent(nb, p, seed):
+    """An independent set A of nb vertices joined to every vertex of an
+    Erdos-Renyi graph H on nb vertices (edge probability p).  Every vertex
+    of A has out-degree nb in the DAG (H's vertices have the higher degree),
+    and the k-cliques are a vertex of A with a (k-1)-clique of H, or a
+    k-clique of H."""
+    rng = np.random.default_rng(seed)
+    A, Bv = np.arange(nb), np.arange(nb, 2 * nb)
+    join = np.stack(np.meshgrid(A, Bv, indexing="ij"), -1).reshape(-1, 2)
+    iu = np.triu_indices(nb, 1)
+    keep = rng.random(len(iu[0])) < p
+    h_edges = np.stack([iu[0][keep], iu[1][keep]], 1)
+    g = gg.from_edges(2 * nb, np.concatenate([join, h_edges + nb]), f"join{nb}_p{p}")
+    return g, gg.from_edges(nb, h_edges, f"H{nb}_p{p}")
+
+
+@pytest.mark.parametrize("smem_degree", [1024, 256])
+def test_bitset_deep(smem_degree):
+    """k = 6..10 on the bitset engine (the depth-first walk over bit rows):
+    every out-degree bucket, rows in shared and in global memory, exact
+    counts and per-level sizes against the oracle, closed forms, and the
+    level-list engine on the same graph."""
+    import itertools
+    import math
+
+    pgm.pgm_set_options(clique_engine=2, bitset_smem_degree=smem_degree)
+    try:
+        for g, ks in [(gg.rmat(1 << 12, 40000, seed=42), (6, 7, 8, 9)),
+                      (gg.barabasi_albert(3000, 9, seed=41), (6, 7, 8, 9, 10))]:
+            assert gpu_cliques(g, ks) == [oracle.clique_count(g, k, "degree", threads=8) for k in ks], g.name
+        assert gpu_cliques(gg.complete(40), range(6, 11)) == [math.comb(40, k) for k in range(6, 11)]
+        sizes = (12,) * 9  # out-degrees up to 96
+        want = [sum(math.prod(c) for c in itertools.combinations(sizes, k)) for k in (6, 7, 8)]
+        assert gpu_cliques(gg.complete_multipartite(sizes), [6, 7, 8]) == want
+        # out-degrees 200 / 400 / 900 / 1100: the 256, 512, 1024 and global-row buckets
+        for nb, p in [(200, 0.3), (400, 0.2), (900, 0.12), (1100, 0.1)]:
+            g, h = _join_independent(nb, p, seed=nb)
+            hc = [oracle.clique_count(h, k, "id", threads=8) for k in (5, 6, 7)]
+            assert gpu_cliques(g, [6, 7]) == [nb * hc[0] + hc[1], nb * hc[1] + hc[2]], g.name
+        # per-level sizes of one count
+        g = gg.rmat(1 << 12, 40000, seed=42)
+        pgm.pgm_set_options(clique_engine=2, bitset_smem_degree=smem_degree, profile=1)
+        with pgm.Graph(g) as G:
+            G.kcliques(8)
+            sizes = pgm.pgm_last_profile()["level_size"]
+        assert sizes[1:9] == oracle.clique_levels(g, 8, "degree", threads=8)[1:9]
+    finally:
+        pgm.pgm_set_options(clique_engine=0, bitset_smem_degree=1024, profile=0)
+    pgm.pgm_set_options(clique_engine=1)
+    try:
+        g = gg.rmat(1 << 12, 40000, seed=42)
+        assert gpu_cliques(g, [6, 7]) == [oracle.clique_count(g, k, "degree", threads=8) for k in (6, 7)]
+    finally:
+        pgm.pgm_set_options(clique_engine=0)
