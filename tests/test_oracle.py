@@ -398,3 +398,35 @@ def test_p5_relabel_invariance_and_roots():
     assert oracle.esu_motifs(gg.relabel(g, perm), 5) == oracle.esu_motifs(g, 5)
     parts = [oracle.esu_motifs(g, 5, roots=r) for r in ((0, 100), (100, 101), (101, 300))]
     assert [sum(x) for x in zip(*parts)] == oracle.esu_motifs(g, 5)
+
+
+def test_large_k_cliques():
+    """k = 8..10 (the deepest levels the library counts): closed forms for
+    complete and complete multipartite graphs, brute force (k = 8) and
+    ID-order / degree-order agreement on dense small random graphs, and the join of an independent set A with a graph H,
+    whose k-cliques are |A| * c_{k-1}(H) + c_k(H)."""
+    for n in (10, 12, 14):
+        g = gg.complete(n)
+        for k in (8, 9, 10):
+            assert oracle.clique_count(g, k, "id") == C(n, k)
+            assert oracle.clique_count(g, k, "degree") == C(n, k)
+    sizes = (2, 3, 2, 3, 2, 3, 2, 3, 2, 3, 1)
+    g = gg.complete_multipartite(sizes)
+    for k in (8, 9, 10):
+        assert oracle.clique_count(g, k, "degree") == e_sym(sizes, k), k
+    for seed in range(20):  # brute force goes to k = 8; ID and degree order agree beyond
+        g = gg.erdos_renyi(14, 0.85, seed=500 + seed)
+        assert oracle.clique_count(g, 8, "id") == oracle.bf_cliques(g, 8), seed
+        for k in (8, 9, 10):
+            assert oracle.clique_count(g, k, "id") == oracle.clique_count(g, k, "degree"), (seed, k)
+    rng = np.random.default_rng(7)
+    nb = 30
+    iu = np.triu_indices(nb, 1)
+    keep = rng.random(len(iu[0])) < 0.6
+    h_edges = np.stack([iu[0][keep], iu[1][keep]], 1)
+    h = gg.from_edges(nb, h_edges)
+    join = np.stack(np.meshgrid(np.arange(nb), np.arange(nb, 2 * nb), indexing="ij"), -1).reshape(-1, 2)
+    g = gg.from_edges(2 * nb, np.concatenate([join, h_edges + nb]))
+    for k in (6, 8, 10):
+        want = nb * oracle.clique_count(h, k - 1, "id") + oracle.clique_count(h, k, "id")
+        assert oracle.clique_count(g, k, "degree") == want, k
