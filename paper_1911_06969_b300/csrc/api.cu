@@ -210,6 +210,7 @@ void Workspace::release_all() {
   ctr.release();
   scan_tmp.release();
   scratch.release();
+  tri.release();
 }
 
 }  // namespace pgm

@@ -115,6 +115,7 @@ struct Workspace {
   DevArr<unsigned long long> ctr;    // queue counters + accumulators
   DevArr<int64_t> scan_tmp;          // block partials of the scan
   DevArr<int32_t> scratch;           // per-warp spill lists of the hub kernels
+  DevArr<uint2> tri;                 // motifs: per-arc triangle counts of the level-2 edges
   void release_all();
 };
 

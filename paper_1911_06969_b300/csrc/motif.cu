@@ -48,24 +48,6 @@ constexpr uint32_t kVidMask = (1u << 30) - 1u;
 constexpr uint32_t kA02 = 1u << 30;
 constexpr uint32_t kA12 = 1u << 31;
 
-// 4-vertex pattern of a 3-embedding with memo (a02, a12) (edge v0-v1
-// always present) plus a vertex with adjacency mask M (bit j = adjacent to
-// v_j); -1 if M = 0.  Order: 3-star, 4-path, tailed-triangle, 4-cycle,
-// diamond, 4-clique.
-__device__ __forceinline__ int pattern4(int a02, int a12, int M) {
-  const int m0 = M & 1, m1 = (M >> 1) & 1, m2 = (M >> 2) & 1;
-  const int d0 = 1 + a02 + m0, d1 = 1 + a12 + m1, d2 = a02 + a12 + m2, d3 = m0 + m1 + m2;
-  const int edges = 1 + a02 + a12 + d3;
-  const int dm = max(max(d0, d1), max(d2, d3));
-  if (d3 == 0) return -1;
-  switch (edges) {
-    case 3: return dm == 3 ? 0 : 1;
-    case 4: return dm == 3 ? 2 : 3;
-    case 5: return 4;
-    default: return 5;
-  }
-}
-
 struct MotifArgs {
   const int32_t* rp;   // undirected CSR
   const int32_t* col;
@@ -94,9 +76,13 @@ struct MotifArgs {
   const int32_t* hub_idx;   // vertex -> hub bitmap row or -1
   const uint32_t* hub_bits; // adjacency bitmaps of hub vertices
   int64_t hub_words;        // words per bitmap row
-  int rev_ratio;            // reverse scan when d(v2) > rev_ratio * (|A| + |B|)
   uint32_t* hubctr;         // level 2, counting modes: next 32-entry batch of each hub vertex
   const int32_t* rev;       // rev[a] = index of the reverse arc of arc a
+  // per arc a = (v0, v1), v1 > v0 (index a - a_base): |N(v1) & A(v0)| and
+  // |N(v1) & A(v0) & (v1, inf)| (triangles on the arc above v0 / above v1),
+  // written by the level-3 inspection, read by the last level (memoised
+  // per level-2 edge, Sec. 4.2, instead of recomputed per level-3 entry)
+  uint2* tri;
 };
 
 template <int N>
@@ -111,12 +97,6 @@ __device__ __forceinline__ void flush_patterns(const MotifArgs& P, long long (&c
     }
     c[i] = 0;
   }
-}
-
-template <int N>
-__device__ __forceinline__ void add_pat(long long (&c)[N], int p, long long d) {
-#pragma unroll
-  for (int i = 0; i < N; i++) c[i] += (i == p) ? d : 0;
 }
 
 // Membership of w in a sorted list, or by one bit of a hub's adjacency
@@ -249,6 +229,7 @@ __device__ __forceinline__ void l2_count_batch(const MotifArgs& P, const int32_t
   const int excl = incl - len;
   if (MODE == mCount) {
     wcnt[lane] = 0;
+    wcnt[32 + lane] = 0;
     __syncwarp();
   }
   for (int base = 0; base < total; base += 32) {
@@ -284,18 +265,25 @@ __device__ __forceinline__ void l2_count_batch(const MotifArgs& P, const int32_t
       }
     } else {
       const unsigned b = __ballot_sync(kFull, in);
+      const unsigned bg = __ballot_sync(kFull, in && x > v1q);
       const int first = max(eq - base, 0);
       const unsigned from_first = ~((1u << first) - 1u);
       const unsigned upto_me = lane == 31 ? kFull : ((2u << lane) - 1u);
       const int qn = __shfl_down_sync(kFull, q, 1);
       const bool last = active && (lane == 31 || t + 1 >= total || qn != q);
       __syncwarp();
-      if (last) wcnt[q] += __popc(b & from_first & upto_me);
+      if (last) {
+        wcnt[q] += __popc(b & from_first & upto_me);
+        wcnt[32 + q] += __popc(bg & from_first & upto_me);
+      }
       __syncwarp();
     }
   }
   if (MODE == mCount) {
-    if (valid) P.cnt[arc0 + j] = (uint32_t)(s - j - 1) + (uint32_t)nbj - wcnt[lane];
+    if (valid) {
+      P.cnt[arc0 + j] = (uint32_t)(s - j - 1) + (uint32_t)nbj - wcnt[lane];
+      P.tri[arc0 + j] = make_uint2(wcnt[lane], wcnt[32 + lane]);
+    }
     __syncwarp();
   }
 }
@@ -316,8 +304,8 @@ template <int MODE>
 __global__ void __launch_bounds__(512, 2) motif_l2_warp(MotifArgs P) {
   extern __shared__ int32_t smem[];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  int32_t* A = smem + wid * (P.cap + 32);
-  uint32_t* wcnt = reinterpret_cast<uint32_t*>(A + P.cap);
+  int32_t* A = smem + wid * (P.cap + 64);
+  uint32_t* wcnt = reinterpret_cast<uint32_t*>(A + P.cap);  // 64 counters
   long long c[2] = {0, 0};
   unsigned long long seen = 0;
   int cur_g = -1;
@@ -371,7 +359,7 @@ __global__ void __launch_bounds__(512, 2) motif_l2_warp(MotifArgs P) {
 // exhausted.
 template <int MODE>
 __global__ void __launch_bounds__(256) motif_l2_hubs(MotifArgs P) {
-  __shared__ uint32_t wcnt_all[8][32];
+  __shared__ uint32_t wcnt_all[8][64];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   uint32_t* wcnt = wcnt_all[wid];
   long long c[2] = {0, 0};
@@ -417,7 +405,7 @@ __global__ void __launch_bounds__(512, 2) motif_l2_block(MotifArgs P) {
   __shared__ long long sh_idx;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   int32_t* stage = smem;
-  uint32_t* wcnt = reinterpret_cast<uint32_t*>(smem + P.block_cap) + wid * 32;
+  uint32_t* wcnt = reinterpret_cast<uint32_t*>(smem + P.block_cap) + wid * 64;
   long long c[2] = {0, 0};
   unsigned long long seen = 0;
   int cur_g = -1;
@@ -459,97 +447,167 @@ __global__ void __launch_bounds__(512, 2) motif_l2_block(MotifArgs P) {
 
 // ------------------------------------------------------------- level 3 (last)
 
-// Membership of w in both lists at once: hub bitmaps where the owner has
-// one, otherwise the two binary searches advance in the same loop (their
-// loads are independent, so they overlap).
-__device__ __forceinline__ void member2(const int32_t* A, int s, int hA, const int32_t* B, int nb, int hB,
-                                        const MotifArgs& P, int32_t w, bool& ia, bool& ib) {
-  int ba = 0, na = s, bb = 0, nbb = nb;
-  if (hA >= 0) na = 0;
-  if (hB >= 0) nbb = 0;
-  while (na > 1 || nbb > 1) {
-    if (na > 1) {
-      const int h = na >> 1;
-      ba = A[ba + h] < w ? ba + h : ba;
-      na -= h;
-    }
-    if (nbb > 1) {
-      const int h = nbb >> 1;
-      bb = B[bb + h] < w ? bb + h : bb;
-      nbb -= h;
-    }
-  }
-  // the lower bound of w is ba or ba + 1 (and bb or bb + 1)
-  ia = hA >= 0 ? ((P.hub_bits[(int64_t)hA * P.hub_words + (w >> 5)] >> (w & 31)) & 1u) != 0
-               : (s > 0 && (A[ba] == w || (ba + 1 < s && A[ba + 1] == w)));
-  ib = hB >= 0 ? ((P.hub_bits[(int64_t)hB * P.hub_words + (w >> 5)] >> (w & 31)) & 1u) != 0
-               : (nb > 0 && (B[bb] == w || (bb + 1 < nb && B[bb + 1] == w)));
-}
-
-// Contribution of one candidate w (adjacency bits a, b, c to v0, v1, v2) of
-// the 3-embedding with memo (a02, a12), given that w is adjacent to v2:
-// the canonical test accepts it (region thresholds of the header comment)
-// and its pattern is counted; the rank-based count of its (a, b) region,
-// which included it, is corrected.
-__device__ __forceinline__ void add_c_region(long long (&c)[6], int a02, int a12, int a, int b,
-                                             int32_t w, int32_t v2) {
-  const int M = 4 | a | (b << 1);
-  if (!a && !b) {
-    add_pat<6>(c, pattern4(a02, a12, 4), 1);
-  } else if (a02) {
-    if (!a || w > v2) {  // adjacent to v0: needs w > v2; to v1 only: always
-      add_pat<6>(c, pattern4(1, a12, M), 1);
-      add_pat<6>(c, pattern4(1, a12, M & 3), -1);
-    }
-  } else if (!a && w > v2) {  // f2 = 1: adjacent to v1 (and v2) only, above v2
-    add_pat<6>(c, pattern4(0, 1, M), 1);
-    add_pat<6>(c, pattern4(0, 1, M & 3), -1);
-  }
-}
-
-// Per-warp filter of the last level: one-hash bitmap over A u B (at most
-// kMFilterW words); a clear bit proves that w is in neither list.
+// Per-warp filters of the last level: one-hash bitmaps of at most kMFilterW
+// words over A and over B; a clear bit proves that w is not in the list.
 constexpr int kMFilterW = 256;
 
 __device__ __forceinline__ uint32_t mf_hash(int32_t x, int shift) {
   return ((uint32_t)x * 0x9E3779B1u) >> shift;
 }
 
-// Shared memory of motif_l3_edge per warp, in ints: A, B, I staging,
-// filter, candidate queue (64 vertices + 64 child lanes), 4 region
-// counters per child of the current batch of 32.
-__host__ __device__ constexpr int64_t ml3_warp_ints(int cap) { return 3LL * cap + kMFilterW + 128 + 128; }
+// words of a filter for `count` keys, about `bits_per_key` bits each (a
+// power of two in [32, kMFilterW]), and the hash shift that spans its bits
+__device__ __forceinline__ int mf_words(int count, int bits_per_key) {
+  int fw = 32;
+  while (fw < kMFilterW && 32LL * fw < (long long)bits_per_key * count) fw <<= 1;
+  return fw;
+}
+__device__ __forceinline__ int mf_shift(int fw) { return 32 - (__ffs(fw) - 1) - 5; }
+
+__device__ __forceinline__ void mf_build(uint32_t* F, int fw, int shift, const int32_t* X, int nx, int lane) {
+  for (int i = lane; i < fw; i += 32) F[i] = 0u;
+  __syncwarp();
+  for (int i = lane; i < nx; i += 32) {
+    const uint32_t h = mf_hash(X[i], shift);
+    atomicOr(F + (h >> 5), 1u << (h & 31));
+  }
+}
+
+__device__ __forceinline__ bool mf_test(const uint32_t* F, int shift, int32_t w) {
+  const uint32_t h = mf_hash(w, shift);
+  return ((F[h >> 5] >> (h & 31)) & 1u) != 0;
+}
+
+__device__ __forceinline__ bool row_bit(const uint32_t* row, int32_t w) {
+  return ((row[w >> 5] >> (w & 31)) & 1u) != 0;
+}
+
+// Shared memory of motif_l3_edge per warp, in ints: candidate queue (64
+// 8-byte entries), 32 lane slots, the two filters, A, B, I staging; an even
+// count keeps every warp's queue 8-byte aligned.
+__host__ __device__ constexpr int64_t ml3_warp_ints(int cap) {
+  return (128 + 32 + 2 * kMFilterW + 3LL * cap + 1) & ~1LL;
+}
+
+// Flattened scan of up to 32 sorted lists, one per lane (col[start ..
+// start + len)), on the whole warp.  The lanes with a non-empty list move
+// to the low lanes (their two tags with them); the slots of all lists are
+// visited 32 at a time, the owner of slot b + lane being the owner of slot
+// b plus the lists that start in slots b + 1 .. b + lane (one OR-reduce
+// per 32 slots).  `test(w)` returns 0 (not a candidate) or 1 | knowledge
+// bits << 1; candidates are queued and handed to `hit(entry, ok, tag0,
+// tag1)` 32 at a time with the tags of their list (entry = w | (list lane
+// | knowledge << 5) << 32), so the exact tests run on full warps.
+template <class Test, class Hit>
+__device__ __forceinline__ void flat_scan(const int32_t* __restrict__ col, int len, int start, int tag0, int tag1,
+                                          unsigned long long* Qe, int32_t* Qs, int lane, Test test, Hit hit) {
+  const unsigned lt = (1u << lane) - 1u;
+  const unsigned nem = __ballot_sync(kFull, len > 0);
+  if (!nem) return;
+  const int nch = __popc(nem);
+  if (len > 0) Qs[__popc(nem & lt)] = lane;
+  __syncwarp();
+  const int src = lane < nch ? Qs[lane] : lane;
+  __syncwarp();
+  const int ct0 = __shfl_sync(kFull, tag0, src);
+  const int ct1 = __shfl_sync(kFull, tag1, src);
+  const int clen = __shfl_sync(kFull, len, src) * (lane < nch);
+  const int cstart = __shfl_sync(kFull, start, src);
+  const int incl = warp_inclusive_scan(clen, lane);
+  const int total = __shfl_sync(kFull, incl, 31);
+  const int excl = incl - clen;
+  const int coff = cstart - excl;  // slot t of this lane's list reads col[coff + t]
+  int qn = 0, q0 = 0;
+  auto drain = [&](int valid) {
+    __syncwarp();
+    const unsigned long long e = Qe[lane];
+    const int q = (int)(e >> 32) & 31;
+    const int t0 = __shfl_sync(kFull, ct0, q), t1 = __shfl_sync(kFull, ct1, q);
+    hit(e, lane < valid, t0, t1);
+    __syncwarp();
+  };
+  constexpr int kU = 4;  // chunks of 32 slots whose loads are issued together
+  for (int base = 0; base < total; base += 32 * kU) {
+    int32_t wv[kU];
+    int qv[kU];
+#pragma unroll
+    for (int r = 0; r < kU; r++) {
+      const int b = base + 32 * r;
+      const int p = excl - b;
+      const unsigned S = __reduce_or_sync(kFull, (lane < nch && p >= 1 && p <= 32) ? (1u << (p - 1)) : 0u);
+      const int q = (q0 + __popc(S & lt)) & 31;
+      q0 += __popc(S);
+      const int t = b + lane;
+      const int oq = __shfl_sync(kFull, coff, q);
+      wv[r] = t < total ? col[oq + t] : -1;
+      qv[r] = q;
+    }
+#pragma unroll
+    for (int r = 0; r < kU; r++) {
+      const int32_t w = wv[r];
+      const int tr = w >= 0 ? test(w) : 0;
+      const unsigned bal = __ballot_sync(kFull, tr != 0);
+      if (tr)
+        Qe[qn + __popc(bal & lt)] =
+            (unsigned long long)(uint32_t)w | ((unsigned long long)(qv[r] | ((tr >> 1) << 5)) << 32);
+      qn += __popc(bal);
+      if (qn >= 32) {
+        drain(32);
+        if (lane < qn - 32) Qe[lane] = Qe[lane + 32];
+        qn -= 32;
+        __syncwarp();
+      }
+    }
+  }
+  if (qn) drain(qn);
+}
 
 // One level-2 edge (v0, v1) per warp at a time, taken from a device queue
 // over arcs, so heavy edges of hub vertices spread over the whole GPU.
 // A = N(v0) & (v0, inf), B = N(v1) & (v0, inf) are staged in shared memory
 // when short (else read in place, with hub bitmaps for membership);
-// I = A & B is built once per edge for the rank queries, and a bitmap
-// filter over A u B once per edge for the scans.
+// I = A & B is built once per edge for the rank queries.
 //
-// For each child (v2, memo), 32 children at a time (one per lane): the
-// candidates not adjacent to v2 are counted by rank queries on A, B and I;
-// the candidates adjacent to v2 (w in N(v2), w > v0, w != v1) are first
-// all counted as "adjacent to v2 only" (a rank query on N(v2)), then the
-// ones that are also in A or B are moved to their regions.  Those are found
-// either forward -- scan N(v2) above v0, keep the elements that pass the
-// filter, queue them and test them exactly in A and B 32 at a time -- or in
-// reverse when N(v2) is much longer than A and B (scan A and B, test each
-// element in N(v2)).
+// The 4th vertex w of a child (v0, v1, v2) falls in one of seven regions
+// M = (w~v0, w~v1, w~v2); the canonical test (header comment) accepts a
+// region's members above a threshold, and the pattern is a function of
+// (a02, a12, M).  So the reduce needs region sizes, not the candidates:
+//
+// f2 = 0 children are A[j+1 .. s) (v1 = A[j]), the first s - j - 1 entries
+// of the edge's segment, so v2's rank in A is its position; the parts of
+// the regions that depend on (v0, v2) only -- |N(v2) & A| and
+// |N(v2) & A & (v2, inf)| -- are memoised per arc by the inspection pass.
+// What is left are the common neighbours w of v1 and v2 above v0: w in
+// A & B above v2, or w in B \ A.  They are found from the side of w: every
+// w in B is extended by N(w) & (v1, w) (w in A) or N(w) & (v1, inf) (w not
+// in A), and each element v2 in A is such a pair (with a12 = v2 in B).
+// This scans the short lists of B's members once per edge instead of
+// N(v2) once per child.  Every other region size is a rank in A, B or I.
+//
+// f2 = 1 children (v2 in B \ A): the elements of N(v2) & (v0, inf) are
+// tested in A and B; the ones in A or B leave the "adjacent to v2 only"
+// region, and those in B \ A above v2 move to region (v1, v2).
+//
+// Both scans run flattened over 32 lists; elements pass a filter (hub
+// bitmap row or shared-memory bitmap filter of A / B) and the survivors are
+// tested exactly, 32 at a time.  Region moves are counted per lane as
+// events and folded into the six pattern counters once per edge.
 constexpr int kML3Threads = 256;  // block size of the last level (at most)
+constexpr int kML3Cap = 256;      // staging capacity (ints per list per warp) of the last level
 
-__global__ void __launch_bounds__(kML3Threads, 3) motif_l3_edge(MotifArgs P) {
-  extern __shared__ int32_t smem[];
+__global__ void __launch_bounds__(kML3Threads, 4) motif_l3_edge(MotifArgs P) {
+  extern __shared__ __align__(16) int32_t smem[];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const unsigned lt = (1u << lane) - 1u;
   const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  int32_t* Abuf = smem + (int64_t)wid * ml3_warp_ints(P.cap);
+  int32_t* wbase = smem + (int64_t)wid * ml3_warp_ints(P.cap);
+  unsigned long long* Qe = reinterpret_cast<unsigned long long*>(wbase);  // candidate queue
+  int32_t* Qs = wbase + 128;                                              // compaction of lanes
+  uint32_t* FA = reinterpret_cast<uint32_t*>(Qs + 32);
+  uint32_t* FB = FA + kMFilterW;
+  int32_t* Abuf = reinterpret_cast<int32_t*>(FB + kMFilterW);
   int32_t* Bbuf = Abuf + P.cap;
   int32_t* Ismem = Bbuf + P.cap;
-  uint32_t* F = reinterpret_cast<uint32_t*>(Ismem + P.cap);
-  int32_t* Qw = reinterpret_cast<int32_t*>(F + kMFilterW);
-  int32_t* Qq = Qw + 64;
-  int32_t* Cnt = Qq + 64;  // Cnt[4 * q + r]: region counters of child lane q
   int32_t* Iglob = P.scratch + gw * P.scratch_stride;
   long long c[6] = {0, 0, 0, 0, 0, 0};
   unsigned long long seen = 0;
@@ -586,8 +644,7 @@ __global__ void __launch_bounds__(kML3Threads, 3) motif_l3_edge(MotifArgs P) {
         A = P.col + u0;
       }
       const int32_t r0 = P.rp[v1], r1 = P.rp[v1 + 1];
-      int bstart = 0;
-      bstart = P.rev[a] - r0 + 1;  // after v0's own entry in N(v1)
+      const int bstart = P.rev[a] - r0 + 1;  // after v0's own entry in N(v1)
       const int nb = r1 - r0 - bstart;
       const int32_t* B;
       if (nb <= P.cap) {
@@ -596,16 +653,16 @@ __global__ void __launch_bounds__(kML3Threads, 3) motif_l3_edge(MotifArgs P) {
       } else {
         B = P.col + r0 + bstart;
       }
-      // filter over A u B: 32 * fw bits
-      int fw = 32;
-      while (fw < s + nb && fw < kMFilterW) fw <<= 1;
-      const int fshift = 32 - (__ffs(fw) - 1) - 5;
-      for (int i = lane; i < fw; i += 32) F[i] = 0u;
+      const uint32_t* hArow = hA >= 0 ? P.hub_bits + (int64_t)hA * P.hub_words : nullptr;
+      const uint32_t* hBrow = hB >= 0 ? P.hub_bits + (int64_t)hB * P.hub_words : nullptr;
+      const int j1 = (int)(a - u0);  // v1 = A[j1]
+      const int nf0 = s - j1 - 1;    // f2 = 0 children, first in the segment
+      const bool f1any = (ce - cb) > nf0;
+      const int fwA = mf_words(s, 8), shA = mf_shift(fwA);
+      const int fwB = mf_words(nb, 8), shB = mf_shift(fwB);
       __syncwarp();
-      for (int i = lane; i < s + nb; i += 32) {
-        const uint32_t h = mf_hash(i < s ? A[i] : B[i - s], fshift);
-        atomicOr(F + (h >> 5), 1u << (h & 31));
-      }
+      if (!hArow) mf_build(FA, fwA, shA, A, s, lane);
+      if (!hBrow && f1any) mf_build(FB, fwB, shB, B, nb, lane);
       // I = A & B, sorted: scan the shorter list, test membership in the other
       int32_t* I = min(s, nb) <= P.cap ? Ismem : Iglob;
       int ni = 0;
@@ -630,186 +687,118 @@ __global__ void __launch_bounds__(kML3Threads, 3) motif_l3_edge(MotifArgs P) {
       }
       __syncwarp();
       if (lane == 0) seen += (unsigned long long)(nb + s);
-      // children, 32 at a time
+      // region moves found by the scans (per lane): f2 = 0 children with a12
+      // = 0 / 1: common neighbour in A & B above v2 (y1*), in B \ A (y2*);
+      // f2 = 1 children: element in A or B (eh), in B \ A above v2 (er)
+      int y1a = 0, y1b = 0, y2a = 0, y2b = 0, eh = 0, er = 0;
+      // f2 = 0 children: extend every w in B by its neighbours v2 in A above v1
+      // (below w when w is in A); candidates v2 must be in A
+      auto test_inA = [&](int32_t v2) -> int {
+        if (hArow) return row_bit(hArow, v2) ? 3 : 0;  // exact: v2 is in A
+        return mf_test(FA, shA, v2) ? 1 : 0;
+      };
+      auto hit_pair = [&](unsigned long long e, bool ok, int /*w*/, int w_in_A) {
+        if (!ok) return;
+        const int32_t v2 = (int32_t)(uint32_t)e;
+        const bool ia = ((e >> 37) & 1) || member(A, s, -1, P, v2);
+        if (!ia) return;
+        const bool a12 = hBrow ? row_bit(hBrow, v2) : member(B, nb, -1, P, v2);
+        if (w_in_A) {
+          y1a += !a12;
+          y1b += a12;
+        } else {
+          y2a += !a12;
+          y2b += a12;
+        }
+      };
+      for (int w0 = 0; w0 < nb; w0 += 32) {
+        int len = 0, start = 0, w_in_A = 0;
+        int32_t w = 0;
+        if (w0 + lane < nb) {
+          w = B[w0 + lane];
+          w_in_A = hArow ? row_bit(hArow, w) : member(I, ni, -1, P, w);
+          const int32_t rw = P.rp[w];
+          const int dw = P.rp[w + 1] - rw;
+          const int lo = lower_bound_dev(P.col + rw, dw, v1 + 1);
+          const int hi = w_in_A ? lower_bound_dev(P.col + rw, dw, w) : dw;
+          start = rw + lo;
+          len = max(hi - lo, 0);
+        }
+        seen += (unsigned long long)len;
+        flat_scan(P.col, len, start, w, w_in_A, Qe, Qs, lane, test_inA, hit_pair);
+      }
+      // f2 = 1 children: scan N(v2) & (v0, inf); candidates in A or B (not v1)
+      auto test_f1 = [&](int32_t x) -> int {
+        const bool ka = hArow != nullptr, kb = hBrow != nullptr;
+        const bool xa = ka && row_bit(hArow, x), xb = kb && row_bit(hBrow, x);
+        const bool ca = ka ? xa : mf_test(FA, shA, x);
+        const bool cbb = kb ? xb : mf_test(FB, shB, x);
+        if (x == v1 || !(ca || cbb)) return 0;
+        return 1 | (ka << 1) | (xa << 2) | (kb << 3) | (xb << 4);
+      };
+      auto hit_f1 = [&](unsigned long long e, bool ok, int v2q, int) {
+        if (!ok) return;
+        const int32_t x = (int32_t)(uint32_t)e;
+        const unsigned k = (unsigned)(e >> 37);
+        const bool ia = (k & 1) ? ((k >> 1) & 1) != 0 : member(A, s, -1, P, x);
+        const bool ib = (k & 4) ? ((k >> 3) & 1) != 0 : member(B, nb, -1, P, x);
+        eh += ia || ib;
+        er += ib && !ia && x > v2q;
+      };
+      // children, 32 at a time: base region sizes; scans of the f2 = 1 children
       for (int64_t c0 = cb; c0 < ce; c0 += 32) {
         const int64_t ci = c0 + lane;
-        const bool valid = ci < ce;
-        int32_t v2 = 0, a0 = 0, d2 = 0, len = 0, start = 0;
-        int flags = 0, hC = -1;  // flags: bit 0 a02, bit 1 a12, bit 2 reverse
-        if (valid) {
+        int32_t v2 = 0;
+        int len = 0, start = 0;
+        if (ci < ce) {
           const uint32_t e = P.l3[ci];
           v2 = (int32_t)(e & kVidMask);
-          const int a02 = (e & kA02) ? 1 : 0;
           const int a12 = (e & kA12) ? 1 : 0;
-          a0 = P.rp[v2];
-          d2 = P.rp[v2 + 1] - a0;
-          hC = P.hub_idx[v2];
-          // base counts of candidates not adjacent to v2 (rank queries)
+          const int t0 = (int)(ci - cb);
           const long long I_gt2 = ni - lower_bound_dev(I, ni, v2 + 1);  // |I & (v2, inf)|
-          if (a02) {
-            const int ia = lower_bound_dev(A, s, v2);  // v2 = A[ia]
-            const long long A_gt2 = s - ia - 1;        // v1 < v2, so v1 is not counted
-            add_pat<6>(c, pattern4(1, a12, 1), A_gt2 - I_gt2);        // A only, w > v2
-            add_pat<6>(c, pattern4(1, a12, 3), I_gt2);                // A & B, w > v2
-            add_pat<6>(c, pattern4(1, a12, 2), (long long)(nb - ni));  // B only, w > v0
+          if (t0 < nf0) {
+            const int idx = j1 + 1 + t0;  // v2 = A[idx]
+            const int64_t a2 = (int64_t)u0 + idx;
+            const uint2 tr = P.tri[a2 - P.a_base];  // (|N(v2) & A|, |N(v2) & A & (v2, inf)|)
+            const int sl = P.rp[v2 + 1] - (P.rev[a2] + 1);  // |N(v2) & (v0, inf)|
+            // region sizes before the common neighbours of v1 and v2 are moved
+            const long long x1 = (long long)(s - idx - 1) - I_gt2 - (long long)tr.y;  // A only, above v2
+            const long long x24 = (long long)(nb - ni) + sl - (long long)tr.x;        // B only; v2 only
+            const long long x35 = I_gt2 + (long long)tr.y;                           // A & B; A & v2
+            if (a12) {
+              c[2] += x1 + x24;
+              c[4] += x35;
+            } else {
+              c[0] += x1;
+              c[1] += x24;
+              c[2] += x35;
+            }
           } else {
+            const int32_t a0 = P.rp[v2];
+            const int d2 = P.rp[v2 + 1] - a0;
+            const int lo = lower_bound_dev(P.col + a0, d2, v0 + 1);
             const int ib = lower_bound_dev(B, nb, v2 + 1);
-            add_pat<6>(c, pattern4(0, 1, 2), (long long)(nb - ib) - I_gt2);  // B only, w > v2
-          }
-          // every w of N(v2) above v0 except v1 starts as "adjacent to v2 only"
-          const int lo = lower_bound_dev(P.col + a0, d2, v0 + 1);
-          add_pat<6>(c, pattern4(a02, a12, 4), (long long)(d2 - lo - a12));
-          const int rev = (long long)(d2 - lo) > (long long)P.rev_ratio * (long long)(s + nb);
-          flags = a02 | (a12 << 1) | (rev << 2);
-          if (rev) {
-            len = s + nb;
-          } else {
-            len = d2 - lo;
             start = a0 + lo;
+            len = d2 - lo;
+            c[0] += (long long)(nb - ib) - I_gt2;  // B only, above v2 (3-star)
+            c[1] += len - 1;                       // v2 only: N(v2) above v0 but v1 (4-path)
           }
         }
         seen += (unsigned long long)len;
-        const int incl = warp_inclusive_scan(len, lane);
-        const int total = __shfl_sync(kFull, incl, 31);
-        const int excl = incl - len;
-        int qn = 0;  // queued forward candidates (warp-uniform)
-        // region counters of this lane's child: [0] queued elements found in A or B,
-        // [1] in A only and above v2, [2] in A and B and above v2, [3] in B only
-        // (and above v2 when the child is not adjacent to v0)
-#pragma unroll
-        for (int r = 0; r < 4; r++) Cnt[4 * lane + r] = 0;
-        __syncwarp();
-        // exact test of queued candidates w (child lane q, non-decreasing over the
-        // lanes); the counts of each run of equal q are added by its first lane
-        auto process = [&](int32_t w, int q, bool ok) {
-          const int fq = __shfl_sync(kFull, flags, q);
-          const int32_t v2q = __shfl_sync(kFull, v2, q);
-          bool hit = false, r1 = false, r2 = false, r3 = false;
-          if (ok) {
-            bool ia, ib;
-            member2(A, s, hA, B, nb, hB, P, w, ia, ib);
-            const bool gt = w > v2q;
-            hit = ia || ib;
-            r1 = ia && !ib && gt;
-            r2 = ia && ib && gt;
-            r3 = !ia && ib && ((fq & 1) || gt);
-          }
-          const int qq = ok ? q : 32;
-          const int qprev = __shfl_up_sync(kFull, qq, 1);
-          const bool head = ok && (lane == 0 || qprev != qq);
-          const unsigned heads = __ballot_sync(kFull, head) | ~__ballot_sync(kFull, ok);
-          const unsigned bh = __ballot_sync(kFull, hit), b1 = __ballot_sync(kFull, r1);
-          const unsigned b2 = __ballot_sync(kFull, r2), b3 = __ballot_sync(kFull, r3);
-          if (head) {
-            const unsigned after = heads & ~((2u << lane) - 1u);  // heads (or unused lanes) after this one
-            const unsigned upto = after ? ((1u << (__ffs(after) - 1)) - 1u) : 0xffffffffu;
-            const unsigned seg = upto & ~lt;
-            Cnt[4 * q + 0] += __popc(bh & seg);
-            Cnt[4 * q + 1] += __popc(b1 & seg);
-            Cnt[4 * q + 2] += __popc(b2 & seg);
-            Cnt[4 * q + 3] += __popc(b3 & seg);
-          }
-        };
-        // the flattened (child, element) slots, kU chunks of 32 at a time: the
-        // loads of all chunks are issued before their elements are tested
-        constexpr int kU = 4;
-        for (int base = 0; base < total; base += 32 * kU) {
-          int32_t wv[kU];
-          int qv[kU];
-          bool anyrev = false;
-#pragma unroll
-          for (int r = 0; r < kU; r++) {
-            const int t = base + r * 32 + lane;
-            const bool active = t < total;
-            const int q = min(warp_owner(incl, t), 31);
-            const int eq = __shfl_sync(kFull, excl, q);
-            const int fq = __shfl_sync(kFull, flags, q);
-            const int stq = __shfl_sync(kFull, start, q);
-            wv[r] = (active && !(fq & 4)) ? P.col[stq + t - eq] : -1;
-            qv[r] = q;
-            anyrev = anyrev || (active && (fq & 4));
-          }
-#pragma unroll
-          for (int r = 0; r < kU; r++) {
-            const int32_t w = wv[r];
-            const uint32_t h = mf_hash(w, fshift);  // branch-free: w = -1 hashes in range too
-            const bool cand = (w >= 0) & (w != v1) & (((F[h >> 5] >> (h & 31)) & 1u) != 0);
-            const unsigned bal = __ballot_sync(kFull, cand);
-            if (cand) {
-              const int pos = qn + __popc(bal & lt);
-              Qw[pos] = w;
-              Qq[pos] = qv[r];
-            }
-            qn += __popc(bal);
-            if (qn >= 32) {
-              __syncwarp();
-              process(Qw[lane], Qq[lane], true);
-              __syncwarp();
-              if (lane < qn - 32) {
-                Qw[lane] = Qw[lane + 32];
-                Qq[lane] = Qq[lane + 32];
-              }
-              qn -= 32;
-              __syncwarp();
-            }
-          }
-          if (__any_sync(kFull, anyrev)) {
-            // reverse: scan A and B, test each element in N(v2)
-            for (int r = 0; r < kU; r++) {
-              const int t = base + r * 32 + lane;
-              const bool active = t < total;
-              const int q = min(warp_owner(incl, t), 31);
-              const int eq = __shfl_sync(kFull, excl, q);
-              const int fq = __shfl_sync(kFull, flags, q);
-              const int aq = __shfl_sync(kFull, a0, q);
-              const int32_t v2q = __shfl_sync(kFull, v2, q);
-              const int d2q = __shfl_sync(kFull, d2, q);
-              const int hCq = __shfl_sync(kFull, hC, q);
-              if (active && (fq & 4)) {
-                const int tq = t - eq;
-                const int a02q = fq & 1, a12q = (fq >> 1) & 1;
-                int32_t x;
-                int ia, ib;
-                bool skip = false;
-                if (tq < s) {
-                  x = A[tq];
-                  ia = 1;
-                  skip = x == v1 || x == v2q;
-                  ib = skip ? 0 : (member(B, nb, hB, P, x) ? 1 : 0);
-                } else {
-                  x = B[tq - s];
-                  ia = 0;
-                  ib = 1;
-                  skip = x == v2q || member(A, s, hA, P, x);  // A's copy is counted above
-                }
-                if (!skip && member(P.col + aq, d2q, hCq, P, x)) {
-                  add_pat<6>(c, pattern4(a02q, a12q, 4), -1);  // not adjacent to v2 only
-                  add_c_region(c, a02q, a12q, ia, ib, x, v2q);
-                }
-              }
-            }
-          }
-        }
-        __syncwarp();
-        process(Qw[lane], Qq[lane], lane < qn);
-        __syncwarp();
-        if (valid && !(flags & 4)) {
-          const int a12 = (flags >> 1) & 1;
-          add_pat<6>(c, pattern4(flags & 1, a12, 4), -(long long)Cnt[4 * lane]);
-          if (flags & 1) {
-            add_pat<6>(c, pattern4(1, a12, 5), Cnt[4 * lane + 1]);
-            add_pat<6>(c, pattern4(1, a12, 1), -(long long)Cnt[4 * lane + 1]);
-            add_pat<6>(c, pattern4(1, a12, 7), Cnt[4 * lane + 2]);
-            add_pat<6>(c, pattern4(1, a12, 3), -(long long)Cnt[4 * lane + 2]);
-            add_pat<6>(c, pattern4(1, a12, 6), Cnt[4 * lane + 3]);
-            add_pat<6>(c, pattern4(1, a12, 2), -(long long)Cnt[4 * lane + 3]);
-          } else {
-            add_pat<6>(c, pattern4(0, 1, 6), Cnt[4 * lane + 3]);
-            add_pat<6>(c, pattern4(0, 1, 2), -(long long)Cnt[4 * lane + 3]);
-          }
-        }
-        __syncwarp();
+        flat_scan(P.col, len, start, v2, 0, Qe, Qs, lane, test_f1, hit_f1);
       }
+      // fold the region moves into the pattern counters: for a12 = 0 the
+      // regions (A only, B only, A&B, v2 only, A&v2, B&v2, all) are (3-star,
+      // 4-path, tailed triangle, 4-path, tailed triangle, 4-cycle, diamond);
+      // for a12 = 1 (tailed triangle x 2, diamond, tailed triangle, diamond x 2,
+      // 4-clique); for f2 = 1, (B only, v2 only, B&v2) are (3-star, 4-path,
+      // tailed triangle)
+      c[0] += y1a - er;
+      c[1] -= 2LL * y2a + eh;
+      c[2] += y1b - 2LL * (y1a + y2b) + er;
+      c[3] += y2a;
+      c[4] += y1a + y2b - 2LL * y1b;
+      c[5] += y1b;
     }
   }
   flush_patterns<6>(P, c, cur_g, lane);
@@ -858,6 +847,7 @@ struct MotifRun {
     P.hub_bits = g.hub_bits;
     P.hub_words = g.hub_words;
     P.rev = g.rev;
+    P.tri = ws.tri.p;
     return P;
   }
 
@@ -871,8 +861,8 @@ struct MotifRun {
     }
     P.stat = ctr() + kStat + MODE;
     const int threads = o.block_threads;
-    const size_t wsmem = (size_t)(threads / 32) * (cap + 32) * sizeof(int32_t);
-    const size_t bsmem = (size_t)block_cap * sizeof(int32_t) + 16 * 32 * sizeof(uint32_t);
+    const size_t wsmem = (size_t)(threads / 32) * (cap + 64) * sizeof(int32_t);
+    const size_t bsmem = (size_t)block_cap * sizeof(int32_t) + 16 * 64 * sizeof(uint32_t);
     PGM_TRY(smem_attr((const void*)motif_l2_warp<MODE>, 160 * 1024));
     PGM_TRY(smem_attr((const void*)motif_l2_block<MODE>, 160 * 1024));
     const int64_t np = (int64_t)P.v_hi - P.v_lo;
@@ -905,10 +895,10 @@ struct MotifRun {
     P.hub_idx = g.hub_idx;
     P.hub_bits = g.hub_bits;
     P.hub_words = g.hub_words;
-    P.rev_ratio = o.reverse_ratio;
     const int threads = std::min(o.block_threads, kML3Threads);
-    // at most 16384 staged ints per block (option check) + filter, queue, counters: < 227 KB
-    const size_t wsmem = (size_t)(threads / 32) * ml3_warp_ints(cap) * sizeof(int32_t);
+    P.cap = std::min(cap, kML3Cap);
+    // (threads / 32) warps of at most 5.8 KB: four blocks fit an SM
+    const size_t wsmem = (size_t)(threads / 32) * ml3_warp_ints(P.cap) * sizeof(int32_t);
     PGM_TRY(smem_attr((const void*)motif_l3_edge, (int)std::max<size_t>(wsmem, 200 * 1024)));
     int grid = grid_for((const void*)motif_l3_edge, threads, wsmem);
     const int64_t na = P.arc_hi - P.arc_lo;
@@ -942,6 +932,7 @@ struct MotifRun {
     if (E == 0) return PGM_OK;
     PGM_TRY(ws.cnt[2].reserve((size_t)E));
     PGM_TRY(ws.off[2].reserve((size_t)E + 1));
+    PGM_TRY(ws.tri.reserve((size_t)E));
     PGM_TRY_CUDA(cudaMemsetAsync(ws.cnt[2].p, 0, (size_t)E * sizeof(uint32_t), s));
     MotifArgs P = args(v_lo, v_hi);
     P.cnt = ws.cnt[2].p;
