@@ -28,10 +28,16 @@
 // (customised classification, Listing 6 extended to 4 vertices):
 //   3 edges: 3-star (max degree 3) or 4-path; 4 edges: tailed triangle
 //   (max degree 3) or 4-cycle; 5: diamond; 6: 4-clique.
-// Candidates adjacent to v2 are enumerated from N(v2) and looked up in the
-// parent's lists A = N(v0) & (v0, inf) and B = N(v1) & (v0, inf) (binary
-// search, Sec. 5.4); candidates adjacent only to v0 and/or v1 are counted
-// by rank queries on A, B and I = A & B, minus the ones seen in N(v2).
+// The reduce needs only the number of accepted candidates per region, so
+// with A = N(v0) & (v0, inf), B = N(v1) & (v0, inf) and I = A & B:
+// candidates adjacent only to v0 and/or v1 are counted by rank queries on
+// A, B and I; those adjacent to v2 come from |N(v2) & (v0, inf)|, from the
+// triangle counts of arc (v0, v2) memoised by the level-3 inspection (f2 =
+// 0), and from the common neighbours of v1 and v2 above v0, which are
+// enumerated -- from B's side for edges with many f2 = 0 children
+// (motif_l3_pairs), from N(v2) otherwise -- and looked up in A and B (hub
+// bitmaps, filters, binary search, Sec. 5.4).  f2 = 1 children scan N(v2)
+// & (v0, inf) against A and B.
 #include <algorithm>
 #include <cstring>
 
@@ -494,11 +500,12 @@ __host__ __device__ constexpr int64_t ml3_warp_ints(int cap) {
 // to the low lanes (their two tags with them); the slots of all lists are
 // visited 32 at a time, the owner of slot b + lane being the owner of slot
 // b plus the lists that start in slots b + 1 .. b + lane (one OR-reduce
-// per 32 slots).  `test(w)` returns 0 (not a candidate) or 1 | knowledge
-// bits << 1; candidates are queued and handed to `hit(entry, ok, tag0,
+// per 32 slots).  `test(w, tag1)` returns 0 (not a candidate) or 1 |
+// knowledge bits << 1; candidates are queued and handed to `hit(entry, ok, tag0,
 // tag1)` 32 at a time with the tags of their list (entry = w | (list lane
-// | knowledge << 5) << 32), so the exact tests run on full warps.
-template <class Test, class Hit>
+// | knowledge << 5) << 32), so the exact tests run on full warps.  The
+// loads of kU chunks of 32 slots are issued before their tests.
+template <int kU, class Test, class Hit>
 __device__ __forceinline__ void flat_scan(const int32_t* __restrict__ col, int len, int start, int tag0, int tag1,
                                           unsigned long long* Qe, int32_t* Qs, int lane, Test test, Hit hit) {
   const unsigned lt = (1u << lane) - 1u;
@@ -526,7 +533,6 @@ __device__ __forceinline__ void flat_scan(const int32_t* __restrict__ col, int l
     hit(e, lane < valid, t0, t1);
     __syncwarp();
   };
-  constexpr int kU = 4;  // chunks of 32 slots whose loads are issued together
   for (int base = 0; base < total; base += 32 * kU) {
     int32_t wv[kU];
     int qv[kU];
@@ -545,7 +551,8 @@ __device__ __forceinline__ void flat_scan(const int32_t* __restrict__ col, int l
 #pragma unroll
     for (int r = 0; r < kU; r++) {
       const int32_t w = wv[r];
-      const int tr = w >= 0 ? test(w) : 0;
+      const int tg = __shfl_sync(kFull, ct1, qv[r]);
+      const int tr = w >= 0 ? test(w, tg) : 0;
       const unsigned bal = __ballot_sync(kFull, tr != 0);
       if (tr)
         Qe[qn + __popc(bal & lt)] =
@@ -594,8 +601,9 @@ __device__ __forceinline__ void flat_scan(const int32_t* __restrict__ col, int l
 // events and folded into the six pattern counters once per edge.
 constexpr int kML3Threads = 256;  // block size of the last level (at most)
 constexpr int kML3Cap = 256;      // staging capacity (ints per list per warp) of the last level
+constexpr int kFromB = 32;        // edges with at least this many f2 = 0 children find them from B's side
 
-__global__ void __launch_bounds__(kML3Threads, 4) motif_l3_edge(MotifArgs P) {
+__global__ void __launch_bounds__(kML3Threads, 3) motif_l3_edge(MotifArgs P) {
   extern __shared__ __align__(16) int32_t smem[];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const unsigned lt = (1u << lane) - 1u;
@@ -612,6 +620,7 @@ __global__ void __launch_bounds__(kML3Threads, 4) motif_l3_edge(MotifArgs P) {
   long long c[6] = {0, 0, 0, 0, 0, 0};
   unsigned long long seen = 0;
   int cur_g = -1;
+  int32_t staged_v0 = -1;  // A (when staged) and its filter belong to this v0
   const int64_t na = P.arc_hi - P.arc_lo;
   for (;;) {
     unsigned long long p0 = 0;
@@ -636,9 +645,12 @@ __global__ void __launch_bounds__(kML3Threads, 4) motif_l3_edge(MotifArgs P) {
       const int32_t u0 = P.up[v0];
       const int s = P.rp[v0 + 1] - u0;
       const int hA = P.hub_idx[v0], hB = P.hub_idx[v1];
+      const bool restage = v0 != staged_v0;  // consecutive edges of one v0 keep A and its filter
+      staged_v0 = v0;
       const int32_t* A;
       if (s <= P.cap) {
-        for (int i = lane; i < s; i += 32) Abuf[i] = P.col[u0 + i];
+        if (restage)
+          for (int i = lane; i < s; i += 32) Abuf[i] = P.col[u0 + i];
         A = Abuf;
       } else {
         A = P.col + u0;
@@ -661,8 +673,8 @@ __global__ void __launch_bounds__(kML3Threads, 4) motif_l3_edge(MotifArgs P) {
       const int fwA = mf_words(s, 8), shA = mf_shift(fwA);
       const int fwB = mf_words(nb, 8), shB = mf_shift(fwB);
       __syncwarp();
-      if (!hArow) mf_build(FA, fwA, shA, A, s, lane);
-      if (!hBrow && f1any) mf_build(FB, fwB, shB, B, nb, lane);
+      if (!hArow && restage) mf_build(FA, fwA, shA, A, s, lane);
+      if (!hBrow && (f1any || nf0 < kFromB)) mf_build(FB, fwB, shB, B, nb, lane);
       // I = A & B, sorted: scan the shorter list, test membership in the other
       int32_t* I = min(s, nb) <= P.cap ? Ismem : Iglob;
       int ni = 0;
@@ -691,13 +703,187 @@ __global__ void __launch_bounds__(kML3Threads, 4) motif_l3_edge(MotifArgs P) {
       // = 0 / 1: common neighbour in A & B above v2 (y1*), in B \ A (y2*);
       // f2 = 1 children: element in A or B (eh), in B \ A above v2 (er)
       int y1a = 0, y1b = 0, y2a = 0, y2b = 0, eh = 0, er = 0;
-      // f2 = 0 children: extend every w in B by its neighbours v2 in A above v1
-      // (below w when w is in A); candidates v2 must be in A
-      auto test_inA = [&](int32_t v2) -> int {
+      // Children scans, N(v2) & (v0, inf), 32 lists at a time (tags: v2,
+      // f2 = 0 | a12 << 1): always for f2 = 1 children, and for the f2 = 0
+      // children of edges with fewer than kFromB of them (the others' common
+      // neighbours are found from B's side by motif_l3_pairs).  Candidates:
+      // f2 = 0 children, in B; f2 = 1 children, in A or B (not v1).
+      // Knowledge bits: A known, in A, B known, in B.
+      auto test = [&](int32_t x, int tg) -> int {
+        const bool ka = hArow != nullptr, kb = hBrow != nullptr;
+        const bool xa = ka && row_bit(hArow, x), xb = kb && row_bit(hBrow, x);
+        const bool ca = ka ? xa : mf_test(FA, shA, x);
+        const bool cbv = kb ? xb : mf_test(FB, shB, x);
+        const bool cand = (tg & 1) ? cbv : (x != v1) & (ca | cbv);
+        return cand ? (1 | (ka << 1) | (xa << 2) | (kb << 3) | (xb << 4)) : 0;
+      };
+      auto hit = [&](unsigned long long e, bool ok, int t0, int tg) {
+        if (!ok) return;
+        const int32_t x = (int32_t)(uint32_t)e;
+        const unsigned k = (unsigned)(e >> 37);
+        const bool ib = (k & 4) ? ((k >> 3) & 1) != 0 : member(B, nb, -1, P, x);
+        if ((tg & 1) && !ib) return;
+        const bool ia = (k & 1) ? ((k >> 1) & 1) != 0 : member(A, s, -1, P, x);
+        if (tg & 1) {  // common neighbour of v1 and v2 = t0: in A & B above v2, or in B \ A
+          const bool y1 = ia && x > t0, y2 = !ia;
+          if (tg & 2) {
+            y1b += y1;
+            y2b += y2;
+          } else {
+            y1a += y1;
+            y2a += y2;
+          }
+        } else {
+          eh += ia || ib;
+          er += ib && !ia && x > t0;
+        }
+      };
+      const bool from_b = nf0 >= kFromB;
+      for (int64_t next = cb; next < ce; next += 32) {
+        int32_t tag0 = 0;
+        int len = 0, start = 0, tag1 = 0;
+        {
+          const int64_t ci = next + lane;
+          if (ci < ce) {
+            const uint32_t e = P.l3[ci];
+            const int32_t v2 = (int32_t)(e & kVidMask);
+            const int a12 = (e & kA12) ? 1 : 0;
+            const int t0 = (int)(ci - cb);
+            const long long I_gt2 = ni - lower_bound_dev(I, ni, v2 + 1);  // |I & (v2, inf)|
+            tag0 = v2;
+            if (t0 < nf0) {
+              const int idx = j1 + 1 + t0;  // v2 = A[idx]
+              const int64_t a2 = (int64_t)u0 + idx;
+              const uint2 tr = P.tri[a2 - P.a_base];  // (|N(v2) & A|, |N(v2) & A & (v2, inf)|)
+              const int st = P.rev[a2] + 1;           // N(v2) & (v0, inf) starts after (v2, v0)
+              const int sl = P.rp[v2 + 1] - st;
+              // region sizes before the common neighbours of v1 and v2 are moved
+              const long long x1 = (long long)(s - idx - 1) - I_gt2 - (long long)tr.y;  // A only, above v2
+              const long long x24 = (long long)(nb - ni) + sl - (long long)tr.x;        // B only; v2 only
+              const long long x35 = I_gt2 + (long long)tr.y;                           // A & B; A & v2
+              if (a12) {
+                c[2] += x1 + x24;
+                c[4] += x35;
+              } else {
+                c[0] += x1;
+                c[1] += x24;
+                c[2] += x35;
+              }
+              if (!from_b) {
+                start = st;
+                len = sl;
+              }
+              tag1 = 1 | (a12 << 1);
+            } else {
+              const int32_t a0 = P.rp[v2];
+              const int d2 = P.rp[v2 + 1] - a0;
+              const int lo = lower_bound_dev(P.col + a0, d2, v0 + 1);
+              const int ib = lower_bound_dev(B, nb, v2 + 1);
+              start = a0 + lo;
+              len = d2 - lo;
+              c[0] += (long long)(nb - ib) - I_gt2;  // B only, above v2 (3-star)
+              c[1] += len - 1;                       // v2 only: N(v2) above v0 but v1 (4-path)
+            }
+          }
+        }
+        seen += (unsigned long long)len;
+        flat_scan<2>(P.col, len, start, tag0, tag1, Qe, Qs, lane, test, hit);
+      }
+      // fold the region moves into the pattern counters: for a12 = 0 the
+      // regions (A only, B only, A&B, v2 only, A&v2, B&v2, all) are (3-star,
+      // 4-path, tailed triangle, 4-path, tailed triangle, 4-cycle, diamond);
+      // for a12 = 1 (tailed triangle x 2, diamond, tailed triangle, diamond x 2,
+      // 4-clique); for f2 = 1, (B only, v2 only, B&v2) are (3-star, 4-path,
+      // tailed triangle)
+      c[0] += y1a - er;
+      c[1] -= 2LL * y2a + eh;
+      c[2] += y1b - 2LL * (y1a + y2b) + er;
+      c[3] += y2a;
+      c[4] += y1a + y2b - 2LL * y1b;
+      c[5] += y1b;
+    }
+  }
+  flush_patterns<6>(P, c, cur_g, lane);
+  seen = warp_sum(seen);
+  if (lane == 0 && seen) atomicAdd(P.stat, seen);
+}
+
+// The common neighbours of v1 and v2 above v0 for the f2 = 0 children of
+// the level-2 edges (v0, v1) that have at least kFromB of them, found from
+// B's side: every w in B = N(v1) & (v0, inf) is extended by N(w) above v1
+// (below w when w is in A), and each element v2 in A makes the pair (v2, w):
+// w in A & B above v2, or w in B \ A, for the child (v0, v1, v2) with a12 =
+// (v2 in B).  The level-3 list itself is not read: the f2 = 0 children of
+// the edge are A above v1.  Region moves are folded into the six pattern
+// counters exactly as motif_l3_edge folds its own.
+__global__ void __launch_bounds__(kML3Threads, 3) motif_l3_pairs(MotifArgs P) {
+  extern __shared__ __align__(16) int32_t smem[];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int32_t* wbase = smem + (int64_t)wid * ml3_warp_ints(P.cap);
+  unsigned long long* Qe = reinterpret_cast<unsigned long long*>(wbase);
+  int32_t* Qs = wbase + 128;
+  uint32_t* FA = reinterpret_cast<uint32_t*>(Qs + 32);
+  int32_t* Abuf = reinterpret_cast<int32_t*>(FA + 2 * kMFilterW);
+  int32_t* Bbuf = Abuf + P.cap;
+  long long c[6] = {0, 0, 0, 0, 0, 0};
+  unsigned long long seen = 0;
+  int cur_g = -1;
+  int32_t staged_v0 = -1;
+  const int64_t na = P.arc_hi - P.arc_lo;
+  for (;;) {
+    unsigned long long p0 = 0;
+    if (lane == 0) p0 = atomicAdd(P.queue + 4, (unsigned long long)kEdgeGrab);
+    p0 = __shfl_sync(kFull, p0, 0);
+    if ((int64_t)p0 >= na) break;
+    const int64_t pend = min((int64_t)p0 + kEdgeGrab, na);
+    for (int64_t ai = (int64_t)p0; ai < pend; ai++) {
+      const int64_t a = P.arc_lo + ai;
+      const int32_t v0 = P.src[a], v1 = P.col[a];
+      if (v1 < v0) continue;  // arcs to lower neighbours are not level-2 edges
+      const int32_t u0 = P.up[v0];
+      const int s = P.rp[v0 + 1] - u0;
+      const int nf0 = s - (int)(a - u0) - 1;
+      if (nf0 < kFromB) continue;  // motif_l3_edge scans these children itself
+      if (P.gid) {
+        const int g = P.gid[v0];
+        if (g != cur_g) {
+          flush_patterns<6>(P, c, cur_g, lane);
+          cur_g = g;
+        }
+      }
+      const int hA = P.hub_idx[v0], hB = P.hub_idx[v1];
+      const uint32_t* hArow = hA >= 0 ? P.hub_bits + (int64_t)hA * P.hub_words : nullptr;
+      const uint32_t* hBrow = hB >= 0 ? P.hub_bits + (int64_t)hB * P.hub_words : nullptr;
+      const bool restage = v0 != staged_v0;  // consecutive edges of one v0 keep A and its filter
+      staged_v0 = v0;
+      const int32_t* A;
+      if (s <= P.cap) {
+        if (restage)
+          for (int i = lane; i < s; i += 32) Abuf[i] = P.col[u0 + i];
+        A = Abuf;
+      } else {
+        A = P.col + u0;
+      }
+      const int fwA = mf_words(s, 8), shA = mf_shift(fwA);
+      __syncwarp();
+      if (!hArow && restage) mf_build(FA, fwA, shA, A, s, lane);
+      const int32_t r0 = P.rp[v1], r1 = P.rp[v1 + 1];
+      const int bstart = P.rev[a] - r0 + 1;  // after v0's own entry in N(v1)
+      const int nb = r1 - r0 - bstart;
+      const int32_t* B;
+      if (nb <= P.cap) {
+        for (int i = lane; i < nb; i += 32) Bbuf[i] = P.col[r0 + bstart + i];
+        B = Bbuf;
+      } else {
+        B = P.col + r0 + bstart;
+      }
+      __syncwarp();
+      int y1a = 0, y1b = 0, y2a = 0, y2b = 0;
+      auto test = [&](int32_t v2, int) -> int {
         if (hArow) return row_bit(hArow, v2) ? 3 : 0;  // exact: v2 is in A
         return mf_test(FA, shA, v2) ? 1 : 0;
       };
-      auto hit_pair = [&](unsigned long long e, bool ok, int /*w*/, int w_in_A) {
+      auto hit = [&](unsigned long long e, bool ok, int, int w_in_A) {
         if (!ok) return;
         const int32_t v2 = (int32_t)(uint32_t)e;
         const bool ia = ((e >> 37) & 1) || member(A, s, -1, P, v2);
@@ -716,86 +902,19 @@ __global__ void __launch_bounds__(kML3Threads, 4) motif_l3_edge(MotifArgs P) {
         int32_t w = 0;
         if (w0 + lane < nb) {
           w = B[w0 + lane];
-          w_in_A = hArow ? row_bit(hArow, w) : member(I, ni, -1, P, w);
-          const int32_t rw = P.rp[w];
-          const int dw = P.rp[w + 1] - rw;
-          const int lo = lower_bound_dev(P.col + rw, dw, v1 + 1);
-          const int hi = w_in_A ? lower_bound_dev(P.col + rw, dw, w) : dw;
-          start = rw + lo;
-          len = max(hi - lo, 0);
+          w_in_A = hArow ? row_bit(hArow, w) : member(A, s, -1, P, w);
+          // N(w) above v1 starts after the reverse arc (w, v1) of arc (v1, w); below
+          // w it ends at up[w], the first neighbour of w above w
+          start = P.rev[(int64_t)r0 + bstart + w0 + lane] + 1;
+          len = max((w_in_A ? P.up[w] : P.rp[w + 1]) - start, 0);
         }
         seen += (unsigned long long)len;
-        flat_scan(P.col, len, start, w, w_in_A, Qe, Qs, lane, test_inA, hit_pair);
+        flat_scan<4>(P.col, len, start, w, w_in_A, Qe, Qs, lane, test, hit);
       }
-      // f2 = 1 children: scan N(v2) & (v0, inf); candidates in A or B (not v1)
-      auto test_f1 = [&](int32_t x) -> int {
-        const bool ka = hArow != nullptr, kb = hBrow != nullptr;
-        const bool xa = ka && row_bit(hArow, x), xb = kb && row_bit(hBrow, x);
-        const bool ca = ka ? xa : mf_test(FA, shA, x);
-        const bool cbb = kb ? xb : mf_test(FB, shB, x);
-        if (x == v1 || !(ca || cbb)) return 0;
-        return 1 | (ka << 1) | (xa << 2) | (kb << 3) | (xb << 4);
-      };
-      auto hit_f1 = [&](unsigned long long e, bool ok, int v2q, int) {
-        if (!ok) return;
-        const int32_t x = (int32_t)(uint32_t)e;
-        const unsigned k = (unsigned)(e >> 37);
-        const bool ia = (k & 1) ? ((k >> 1) & 1) != 0 : member(A, s, -1, P, x);
-        const bool ib = (k & 4) ? ((k >> 3) & 1) != 0 : member(B, nb, -1, P, x);
-        eh += ia || ib;
-        er += ib && !ia && x > v2q;
-      };
-      // children, 32 at a time: base region sizes; scans of the f2 = 1 children
-      for (int64_t c0 = cb; c0 < ce; c0 += 32) {
-        const int64_t ci = c0 + lane;
-        int32_t v2 = 0;
-        int len = 0, start = 0;
-        if (ci < ce) {
-          const uint32_t e = P.l3[ci];
-          v2 = (int32_t)(e & kVidMask);
-          const int a12 = (e & kA12) ? 1 : 0;
-          const int t0 = (int)(ci - cb);
-          const long long I_gt2 = ni - lower_bound_dev(I, ni, v2 + 1);  // |I & (v2, inf)|
-          if (t0 < nf0) {
-            const int idx = j1 + 1 + t0;  // v2 = A[idx]
-            const int64_t a2 = (int64_t)u0 + idx;
-            const uint2 tr = P.tri[a2 - P.a_base];  // (|N(v2) & A|, |N(v2) & A & (v2, inf)|)
-            const int sl = P.rp[v2 + 1] - (P.rev[a2] + 1);  // |N(v2) & (v0, inf)|
-            // region sizes before the common neighbours of v1 and v2 are moved
-            const long long x1 = (long long)(s - idx - 1) - I_gt2 - (long long)tr.y;  // A only, above v2
-            const long long x24 = (long long)(nb - ni) + sl - (long long)tr.x;        // B only; v2 only
-            const long long x35 = I_gt2 + (long long)tr.y;                           // A & B; A & v2
-            if (a12) {
-              c[2] += x1 + x24;
-              c[4] += x35;
-            } else {
-              c[0] += x1;
-              c[1] += x24;
-              c[2] += x35;
-            }
-          } else {
-            const int32_t a0 = P.rp[v2];
-            const int d2 = P.rp[v2 + 1] - a0;
-            const int lo = lower_bound_dev(P.col + a0, d2, v0 + 1);
-            const int ib = lower_bound_dev(B, nb, v2 + 1);
-            start = a0 + lo;
-            len = d2 - lo;
-            c[0] += (long long)(nb - ib) - I_gt2;  // B only, above v2 (3-star)
-            c[1] += len - 1;                       // v2 only: N(v2) above v0 but v1 (4-path)
-          }
-        }
-        seen += (unsigned long long)len;
-        flat_scan(P.col, len, start, v2, 0, Qe, Qs, lane, test_f1, hit_f1);
-      }
-      // fold the region moves into the pattern counters: for a12 = 0 the
-      // regions (A only, B only, A&B, v2 only, A&v2, B&v2, all) are (3-star,
-      // 4-path, tailed triangle, 4-path, tailed triangle, 4-cycle, diamond);
-      // for a12 = 1 (tailed triangle x 2, diamond, tailed triangle, diamond x 2,
-      // 4-clique); for f2 = 1, (B only, v2 only, B&v2) are (3-star, 4-path,
-      // tailed triangle)
-      c[0] += y1a - er;
-      c[1] -= 2LL * y2a + eh;
-      c[2] += y1b - 2LL * (y1a + y2b) + er;
+      // region moves (see motif_l3_edge): y1 = A & B & v2, y2 = B & v2 (not A)
+      c[0] += y1a;
+      c[1] -= 2LL * y2a;
+      c[2] += y1b - 2LL * (y1a + y2b);
       c[3] += y2a;
       c[4] += y1a + y2b - 2LL * y1b;
       c[5] += y1b;
@@ -887,7 +1006,8 @@ struct MotifRun {
   }
 
   pgm_status launch_l3(MotifArgs P, int32_t pa, int32_t pb, double entries) {
-    PGM_TRY_CUDA(cudaMemsetAsync(ctr() + kQ, 0, 4 * sizeof(unsigned long long), s));
+    // queue slots: [0] motif_l3_edge, [4] motif_l3_pairs
+    PGM_TRY_CUDA(cudaMemsetAsync(ctr() + kQ, 0, 5 * sizeof(unsigned long long), s));
     P.stat = ctr() + kStat + 3;
     P.src = g.src;
     P.arc_lo = g.h_rp[pa];
@@ -900,6 +1020,7 @@ struct MotifRun {
     // (threads / 32) warps of at most 5.8 KB: four blocks fit an SM
     const size_t wsmem = (size_t)(threads / 32) * ml3_warp_ints(P.cap) * sizeof(int32_t);
     PGM_TRY(smem_attr((const void*)motif_l3_edge, (int)std::max<size_t>(wsmem, 200 * 1024)));
+    PGM_TRY(smem_attr((const void*)motif_l3_pairs, (int)std::max<size_t>(wsmem, 200 * 1024)));
     int grid = grid_for((const void*)motif_l3_edge, threads, wsmem);
     const int64_t na = P.arc_hi - P.arc_lo;
     const int64_t blocks_needed = ((na + kEdgeGrab - 1) / kEdgeGrab + threads / 32 - 1) / (threads / 32);
@@ -911,6 +1032,8 @@ struct MotifRun {
     Profiler& prof = profiler();
     int id = prof.begin("extend_sum", 3);
     motif_l3_edge<<<grid, threads, wsmem, s>>>(P);
+    PGM_CHECK_LAUNCH();
+    motif_l3_pairs<<<grid, threads, wsmem, s>>>(P);
     PGM_CHECK_LAUNCH();
     prof.end(id, entries, 0.0);
     return PGM_OK;
