@@ -334,9 +334,11 @@ void pgm_server_destroy(pgm_server *s);
  *   count_dev       device uint64 that receives the count
  * Nothing is allocated: the kernels' scratch (512 B of counters and 8 MiB
  * of hub-parent slots) is a fixed file-scope device array that every GPU
- * loading the library holds until the process exits.  Graphs needing more
- * hub slots than that (m / (hub_threshold + 1) + 2 > 2^20) fail with
- * PGM_EUNSUPPORTED.  The first call on a device looks up the array's device
+ * loading the library holds until the process exits.  Graphs that could
+ * need more hub slots than that fail with PGM_EUNSUPPORTED before any
+ * device work: m / (h + 1) + 2 > 2^20, where h = min(options.hub_threshold,
+ * options.warp_stage_cap) (h = warp_stage_cap while hub_threshold is
+ * unset), the out-degree above which a parent is a hub.  The first call on a device looks up the array's device
  * address (make that first call before any stream capture).  All calls
  * share the one array and clear its counters on entry: calls that overlap
  * on the GPU race and must be serialised by the caller.  Synchronises

@@ -58,3 +58,35 @@ def test_noalloc_rejects_oversize():
     with pytest.raises(pgm.PgmError) as e:
         pgm.pgm_count_triangles_noalloc(10, p, p, 1 << 31, p)
     assert e.value.status == pgm.PGM_EUNSUPPORTED
+
+
+def test_noalloc_bound_follows_effective_hub_threshold():
+    """The size limit uses the hub threshold the kernels apply, h =
+    min(hub_threshold, warp_stage_cap): with warp_stage_cap = 32 and a larger
+    hub_threshold, m = 33 * (2^20 - 2) + 32 arcs is the largest accepted
+    size.  One arc more is rejected before any device work; a DAG of exactly
+    that many arcs (bipartite, so no triangles) is counted."""
+    import torch
+
+    saved = pgm.pgm_get_options()
+    pgm.pgm_set_options(warp_stage_cap=32, hub_threshold=4096)
+    try:
+        limit = 33 * ((1 << 20) - 2) + 32
+        out = torch.full((1,), -1, dtype=torch.int64, device="cuda")
+        p = out.data_ptr()
+        with pytest.raises(pgm.PgmError) as e:
+            pgm.pgm_count_triangles_noalloc(10, p, p, limit + 1, p)
+        assert e.value.status == pgm.PGM_EUNSUPPORTED
+        S = 1 << 15  # sources, each pointing to a prefix of the same 1056 targets
+        deg = np.full(S, limit // S, np.int64)
+        deg[: limit % S] += 1
+        rp = np.zeros(S + 1057, np.int64)
+        rp[1 : S + 1] = np.cumsum(deg)
+        rp[S + 1 :] = limit
+        col = (S + np.arange(limit, dtype=np.int64) - np.repeat(rp[:S], deg)).astype(np.int32)
+        d_rp = torch.tensor(rp.astype(np.int32), device="cuda")
+        d_col = torch.from_numpy(col).to("cuda")
+        pgm.pgm_count_triangles_noalloc(S + 1056, d_rp.data_ptr(), d_col.data_ptr(), limit, out.data_ptr())
+        assert int(out.item()) == 0
+    finally:
+        pgm.pgm_set_options(**saved)
