@@ -1,26 +1,30 @@
 """Benchmark: exact 4-clique counting on R-MAT scale 21 (28,000,000 edges).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--no-extras]
+    python bench.py --sweep [--sweep-scales 20,21,...]      # R-MAT weak-scaling series
 
 A step is one pgm_count_kcliques(g, 4) call on the device-resident, oriented
-graph: level 2 (the DAG) -> inspection -> scan -> level 3 (triangles, written)
--> fused level-4 count.  The metric is embeddings per second: the embeddings
-of every level the step enumerates, |L2| + |L3| + |L4| (edges + triangles +
-4-cliques), divided by the step time.  L2 is flushed (a 256 MiB device write)
-between timed steps, outside the timed events.
+graph: level 2 (the DAG) -> level 3 (triangles, as bit rows) -> fused
+level-4 count.  The metric is embeddings per second: the embeddings of every
+level the step enumerates, |L2| + |L3| + |L4| (edges + triangles +
+4-cliques), divided by the step time.  L2 is flushed (a 256 MiB device
+write) between timed steps, outside the timed events.
 
 Under torchrun (N > 1) each rank counts the part of the 4-cliques whose
-first DAG vertex lies in its share of the vertices (shares balanced by
-sum of squared out-degrees) and the counts are summed at the end (strong
-scaling: the total work is fixed).
+first DAG vertex lies in its share of the vertices (shares balanced by the
+row-building work of the bitset engine, sum over out-arcs u -> v of
+d+(v)), and the per-level counts are summed exactly (uint64, as two 32-bit
+halves) at the end (strong scaling: the total work is fixed).
 
-Extras (N = 1, rank 0; --no-extras skips them): 4-motif counting on the
-Chung-Lu graph (1M vertices, exponent 2.1), and the batched path (20,000
+Extras (N = 1, rank 0; --no-extras skips them): the other configurations
+of the workload set, each with its exactness flag -- triangles on the
+Erdos-Renyi n = 4096 graph, 5-cliques on R-MAT 21, 3- and 4-motifs on the
+Chung-Lu graph (1M vertices, exponent 2.1) -- the batched path (20,000
 small graphs in one pass, replayed as a CUDA graph) against the per-graph
-launch loop.
+launch loop, the serving loop, listing and 5-motifs.
 
 --impl reference times the CPU oracle (as it stands, on all host cores) on a
-bounded sample of the same workload, in the same metric.
+bounded sample of the same workload, in the same metric and config.
 """
 from __future__ import annotations
 
@@ -61,6 +65,12 @@ def peaks():
     if d and d.get("hbm_gbs"):
         return float(d["hbm_gbs"]), "measured"
     return 6400.0, "fallback"
+
+
+def bench_config(g, k, workload):
+    """The workload description both arms print (identical dicts)."""
+    return {"workload": workload, "n": g.n, "m": g.m, "k": k,
+            "l2_flush": "256 MiB device write between steps"}
 
 
 # --------------------------------------------------------------- clocks
@@ -104,40 +114,97 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------ partition
-def vertex_shares(g, world):
-    """Contiguous vertex ranges with about equal sum of squared DAG out-degrees."""
-    if world == 1:
-        return [(0, g.n)]
+def dag_outdeg(g):
+    """Out-degrees of the (degree, ID) orientation, and the arc keep mask."""
     deg = np.diff(g.rowptr)
     src = np.repeat(np.arange(g.n, dtype=np.int64), deg)
     dc = deg[g.col]
     ds = deg[src]
     keep = (ds < dc) | ((ds == dc) & (src < g.col))
-    outdeg = np.bincount(src[keep], minlength=g.n).astype(np.float64)
-    c = np.cumsum(outdeg * outdeg + 1.0)
+    return np.bincount(src[keep], minlength=g.n).astype(np.int64), src, keep
+
+
+def vertex_weights(g):
+    """Work of the bitset engine at each vertex u: the out-lists of its
+    out-neighbours read while its rows are built (sum over u -> v of d+(v)),
+    plus its own out-list and a constant per vertex."""
+    outdeg, src, keep = dag_outdeg(g)
+    w = np.bincount(src[keep], weights=outdeg[g.col[keep]].astype(np.float64), minlength=g.n)
+    return w + outdeg + 1.0
+
+
+def vertex_shares(g, world):
+    """Contiguous vertex ranges of about equal bitset-engine work."""
+    if world == 1:
+        return [(0, g.n)]
+    c = np.cumsum(vertex_weights(g))
     cuts = [0] + [int(np.searchsorted(c, c[-1] * r / world)) for r in range(1, world)] + [g.n]
     return list(zip(cuts[:-1], cuts[1:]))
 
 
+def allreduce_u64(values, dist, device="cpu"):
+    """Exact sum of non-negative integers (< 2^64 each) over the ranks.  Each
+    value travels as two 32-bit halves in int64 slots, so no partial sum can
+    wrap or round for fewer than 2^31 ranks; the halves are recombined on
+    the host with Python integers."""
+    import torch
+
+    halves = []
+    for v in values:
+        v = int(v)
+        halves += [v & 0xFFFFFFFF, v >> 32]
+    t = torch.tensor(halves, dtype=torch.int64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    h = [int(x) for x in t.tolist()]
+    return [h[2 * i] + (h[2 * i + 1] << 32) for i in range(len(values))]
+
+
+def allreduce_max(x, dist, device="cpu"):
+    import torch
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 # ----------------------------------------------------------- oracle legs
-def oracle_sample(g, k, target_s=12.0):
-    """Time the oracle clique enumerator on a bounded root sample; embeddings/s."""
+def oracle_sample(g, k, target_s=12.0, threads=None, roots=None):
+    """The oracle's degree-ordered clique enumerator on a bounded root sample:
+    embeddings of levels 2..k per second of enumeration.  The oracle builds
+    its later-neighbour lists (O(m), single-threaded) on every call; that
+    set-up is timed alone (an empty root range) and subtracted, as the
+    paper's timing excludes preprocessing (Sec. 6.1).  The root range grows
+    until the enumeration alone takes at least half the target (or is the
+    given `roots` count)."""
     import oracle
 
-    threads = os.cpu_count() or 1
-    r = max(1, g.n // 512)
+    threads = threads or os.cpu_count() or 1
     t0 = time.perf_counter()
-    lv = oracle.clique_levels(g, k, "degree", roots=(0, r), threads=threads)
-    t1 = time.perf_counter() - t0
-    if t1 < target_s / 4:
-        r = min(g.n, int(r * target_s / max(t1, 1e-3)))
+    oracle.clique_levels(g, k, "degree", roots=(0, 0), threads=threads)
+    setup = time.perf_counter() - t0
+    r = roots or max(1, g.n // 512)
+    while True:
         t0 = time.perf_counter()
         lv = oracle.clique_levels(g, k, "degree", roots=(0, r), threads=threads)
-        t1 = time.perf_counter() - t0
+        enum = max(time.perf_counter() - t0 - setup, 1e-6)
+        if roots or enum >= target_s / 2 or r >= g.n:
+            break
+        r = min(g.n, max(r + 1, int(r * target_s / enum)))
     emb = sum(lv[2:k + 1])
-    return {"value": emb / t1, "unit": "embeddings/s", "cores": threads, "kind": "oracle",
-            "sample": f"orc_clique_count (degree order, OpenMP) on roots [0, {r}) of {g.n} vertices "
-                      f"({emb} embeddings of levels 2..{k}) in {t1:.2f} s"}
+    return {"value": emb / enum, "unit": "embeddings/s", "cores": threads, "kind": "oracle",
+            "enum_s": enum, "setup_s": setup, "roots": r,
+            "sample": f"orc_clique_count (degree order, {threads} OpenMP threads) on roots [0, {r}) of {g.n} "
+                      f"vertices: {emb} embeddings of levels 2..{k} in {enum:.2f} s of enumeration "
+                      f"({emb / enum:.4g} embeddings/s; the {setup:.2f} s later-list build of each call "
+                      f"is timed alone and excluded)"}
+
+
+def cpu_baselines(g, k):
+    """All host cores (the reported baseline) and one thread beside it."""
+    cb = oracle_sample(g, k, target_s=12.0)
+    one = oracle_sample(g, k, target_s=6.0, threads=1)
+    cb["single_thread"] = {"value": one["value"], "cores": 1, "sample": one["sample"]}
+    return cb
 
 
 def run_reference(args):
@@ -145,22 +212,20 @@ def run_reference(args):
     if rank != 0:
         return 0
     g = gg.rmat21()
-    cb = oracle_sample(g, 4)
-    steps = []
-    for _ in range(args.warmup + args.steps):
-        steps.append(oracle_sample(g, 4, target_s=max(2.0, 60.0 / (args.warmup + args.steps))))
+    # the first sample sizes the root range; every step then enumerates the same roots
+    per_step = max(1.5, 60.0 / (args.warmup + args.steps))
+    first = oracle_sample(g, 4, target_s=per_step)
+    steps = [first] + [oracle_sample(g, 4, roots=first["roots"]) for _ in range(args.warmup + args.steps - 1)]
     timed = steps[args.warmup:]
-    v = float(np.mean([s["value"] for s in timed]))
-    # a full step enumerates |L2| + |L3| + |L4| embeddings; at the sampled rate it would take this long
-    gold = load_json(os.path.join(GOLD, "rmat21.json"))
-    full_emb = float(sum(gold["clique_levels_k4"][2:])) if gold else None
+    emb = sum(s["value"] * s["enum_s"] for s in timed)
+    t = sum(s["enum_s"] for s in timed)
+    v = emb / t
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "embeddings/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": full_emb / v * 1e3 if full_emb else None, "higher_is_better": True,
-            "scaling": "strong", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "sample": timed[-1]["sample"],
-                       "ms_per_step": "projected: the full step's embeddings at the sampled rate"},
-            "cpu_baseline": {**cb, "value": v},
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t / len(timed) * 1e3,
+            "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic", "config": bench_config(g, 4, WORKLOAD),
+            "cpu_baseline": {"value": v, "unit": "embeddings/s", "cores": timed[-1]["cores"], "kind": "oracle",
+                             "sample": "each step: " + timed[-1]["sample"]},
             "e2e": {"value": v, "unit": "embeddings/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -186,11 +251,15 @@ def main(argv=None):
                     help="profiling: time only motif counting (--motif-k) on a graph of N vertices")
     ap.add_argument("--motif-k", type=int, default=4, choices=[3, 4, 5],
                     help="profiling: motif size of --motif-only (3, 4: Chung-Lu graph; 5: G(N, 10/(N-1)))")
+    ap.add_argument("--sweep", action="store_true", help="R-MAT weak-scaling series (average degree 20)")
+    ap.add_argument("--sweep-scales", default="20,21,22,23,24,25")
     args = ap.parse_args(argv)
     if args.impl == "reference":
         return run_reference(args)
     if args.motif_only:
         return motif_only(args)
+    if args.sweep:
+        return sweep(args)
 
     import torch
     import torch.distributed as dist
@@ -207,13 +276,6 @@ def main(argv=None):
     def barrier():
         if world > 1:
             dist.barrier()
-
-    def allreduce(x, op):
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=op)
-        return float(t.item())
 
     full = args.scale == 21 and args.edges == 28_000_000
     g = gg.rmat21() if full else gg.rmat(1 << args.scale, args.edges, seed=1)
@@ -236,7 +298,7 @@ def main(argv=None):
     for _ in range(args.warmup):
         count = step()
     prof = pgm.pgm_last_profile()
-    emb = sum(prof["level_size"][2:k + 1])  # |L2| + ... + |Lk| of this rank's share
+    levels = [int(x) for x in prof["level_size"][: k + 1]]  # this rank's share, |L_l| at index l
 
     clocks = ClockSampler(local)
     barrier()
@@ -266,9 +328,14 @@ def main(argv=None):
     barrier()
     launches = pgm.pgm_kernel_launches() - launches0
     clk = clocks.stop()
-    total_ms = allreduce(sum(ms), dist.ReduceOp.MAX if world > 1 else None)
-    total_emb = allreduce(float(emb), dist.ReduceOp.SUM if world > 1 else None)
-    total_count = int(allreduce(float(count), dist.ReduceOp.SUM if world > 1 else None))
+    if world > 1:
+        dev = torch.device("cuda", local)
+        total_ms = allreduce_max(sum(ms), dist, dev)
+        tot_levels = allreduce_u64(levels, dist, dev)
+    else:
+        total_ms, tot_levels = sum(ms), levels
+    total_emb = sum(tot_levels[2:k + 1])
+    total_count = tot_levels[k]
     pgm.pgm_set_options(profile=0)
 
     if rank != 0:
@@ -280,32 +347,24 @@ def main(argv=None):
     value = total_emb * args.steps / (total_ms * 1e-3)
     gold = load_json(os.path.join(GOLD, "rmat21.json")) if full else None
     exact = None
-    if gold and world == 1:
-        exact = gold["clique_levels_k4"][4] == total_count
-    hbm, peak_kind = peaks()
-    achieved = dom_bytes / (dom_ms * 1e-3) / 1e9 if dom_ms > 0 else None
-    traffic_rec = load_json(os.path.join(ROOT, "profiles", "traffic.json")) or {}
-    traffic = traffic_rec.get(f"{dom}_rmat21_k4") if full else None
+    if gold:
+        exact = gold["clique_levels_k4"][2:] == tot_levels[2:5]
     line = {
         "metric": METRIC, "value": value, "unit": "embeddings/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "strong", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-        "config": {"workload": workload, "n": g.n, "m": g.m, "k": k, "l2_flush": "256 MiB device write between steps",
-                   "embeddings_per_step": total_emb, "count": total_count, "exact_vs_oracle": exact,
-                   "step_ms": [round(x, 3) for x in ms]},
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": achieved / hbm if achieved else None, "traffic": traffic,
-                     "kernel": KERNELS.get(dom, dom),
-                     "kernel_ms_per_launch": dom_ms / max(dom_launches, 1),
-                     "alg_bytes_per_launch": dom_bytes / max(dom_launches, 1), "peak_kind": peak_kind},
+        "config": bench_config(g, k, workload),
+        "result": {"count": total_count, "level_sizes": tot_levels[1:], "embeddings_per_step": total_emb,
+                   "exact_vs_oracle": exact, "step_ms": [round(x, 3) for x in ms]},
+        "roofline": roofline(g, k, dom, dom_ms, dom_bytes, dom_launches, full and world == 1, clk, pgm, torch),
         "gpu_launches": launches,
         "clocks": clk,
     }
     # end to end through the C ABI from pinned host buffers
     if not args.no_e2e:
-        line["e2e"] = e2e(g, pgm, torch, stream, emb)
+        line["e2e"] = e2e(g, pgm, torch, stream, total_emb, steps=args.steps)
     if not args.no_cpu_baseline and world == 1:
-        line["cpu_baseline"] = oracle_sample(g, 4)
+        line["cpu_baseline"] = cpu_baselines(g, 4)
     G.close()
     if not args.no_extras and world == 1 and full:
         line["extras"] = extras(pgm, torch, stream, flush)
@@ -313,6 +372,68 @@ def main(argv=None):
     if world > 1:
         dist.destroy_process_group()
     return 0
+
+
+def roofline(g, k, dom, dom_ms, dom_bytes, dom_launches, full, clk, pgm, torch):
+    """HBM roof of the dominant phase with the scope's per-level algorithmic
+    bytes, and the instruction-issue roof that binds it.
+
+    bytes (level 2 -> 3): every DAG arc u -> v reads N+(v) (4 B per element)
+    and its own record (8 B); every triangle is a level-3 entry written (8 B).
+    The level 3 -> 4 term, sum over triangles (4 d+(last) + 8), is moved
+    between on-chip bit rows by this engine and is reported beside it."""
+    hbm, peak_kind = peaks()
+    kms = dom_ms / max(dom_launches, 1)
+    bpl = dom_bytes / max(dom_launches, 1)
+    achieved = bpl / (kms * 1e-3) / 1e9 if kms > 0 else None
+    traffic_rec = load_json(os.path.join(ROOT, "profiles", "traffic.json")) or {}
+    issue_rec = load_json(os.path.join(ROOT, "profiles", "issue.json")) or {}
+    key = f"{dom}_rmat21_k{k}"
+    r = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+         "frac": achieved / hbm if achieved else None, "peak_kind": peak_kind,
+         "traffic": traffic_rec.get(key) if full else None, "kernel": KERNELS.get(dom, dom),
+         "kernel_ms_per_launch": kms, "alg_bytes_per_launch": bpl,
+         "alg_bytes_rule": "sum over DAG arcs u->v of (4 d+(v) + 8) + 8 |L3| (level 2 -> 3)"}
+    if full:
+        s3 = level3_last_outdeg_sum(g, pgm, torch)
+        if s3 is not None:
+            l3 = s3["triangles"]
+            r["alg_bytes_l3_to_l4_per_launch"] = 4.0 * s3["sum_outdeg_last"] + 8.0 * l3
+            r["alg_bytes_l3_to_l4_note"] = ("sum over triangles of (4 d+(last) + 8); on-chip bit rows here, "
+                                           "not HBM traffic")
+    inst = issue_rec.get(key) if full else None
+    if inst and kms > 0 and clk.get("sm_mhz"):
+        sms = torch.cuda.get_device_properties(0).multi_processor_count
+        peak_issue = sms * 4 * clk["sm_mhz"] * 1e6  # one warp instruction per scheduler per cycle
+        ach = inst / (kms * 1e-3)
+        r["issue"] = {"achieved": ach, "peak": peak_issue, "unit": "warp instructions/s",
+                      "frac": ach / peak_issue, "inst_per_launch": inst,
+                      "peak_rule": f"{sms} SMs x 4 schedulers x {clk['sm_mhz']:.0f} MHz (median sampled clock)"}
+    return r
+
+
+def level3_last_outdeg_sum(g, pgm, torch):
+    """Sum over the triangles (level-3 embeddings u -> v -> w) of d+(w): the
+    triangles are listed once into a device buffer (rows in DAG order) and
+    reduced with torch, outside the timed region."""
+    outdeg, _, _ = dag_outdeg(g)
+    h = pgm.pgm_graph_create_csr(g.n, g.rowptr, g.col)
+    try:
+        n = pgm.pgm_list_kcliques(h, 3)
+        free, _ = torch.cuda.mem_get_info()
+        if n * 12 + (g.n * 8) > free * 0.8:
+            return None
+        buf = torch.empty((n, 3), dtype=torch.int32, device="cuda")
+        pgm.pgm_list_kcliques(h, 3, buf.data_ptr(), n)
+        d = torch.from_numpy(outdeg).to("cuda")
+        s = 0
+        step = 1 << 26
+        for i in range(0, n, step):
+            s += int(d[buf[i:i + step, 2].long()].sum().item())
+        del buf
+        return {"triangles": n, "sum_outdeg_last": s}
+    finally:
+        pgm.pgm_graph_destroy(h)
 
 
 def motif_only(args):
@@ -346,7 +467,7 @@ def motif_only(args):
     return 0
 
 
-def e2e(g, pgm, torch, stream, emb, steps=2):
+def e2e(g, pgm, torch, stream, emb, steps=5):
     rp = torch.from_numpy(g.rowptr).pin_memory()
     col = torch.from_numpy(g.col).pin_memory()
     rpn, coln = rp.numpy(), col.numpy()
@@ -366,13 +487,53 @@ def e2e(g, pgm, torch, stream, emb, steps=2):
     # h2d: int64 row pointers + int32 columns; d2h: the status words of upload (24 B) and
     # orientation (16 B) and the counter block of the count (20 x 8 B)
     return {"value": emb / t, "unit": "embeddings/s", "h2d_bytes_per_step": (g.n + 1) * 8 + g.narcs * 4,
-            "d2h_bytes_per_step": 24 + 16 + 160, "ms_per_step": t * 1e3, "count": c,
+            "d2h_bytes_per_step": 24 + 16 + 160, "ms_per_step": t * 1e3, "steps": steps,
+            "ms_min": min(ts) * 1e3, "count": c,
             "includes": "graph upload from pinned host CSR, orientation, count, result readback"}
+
+
+def timed_calls(fn, stream, torch, flush=None, reps=3):
+    """Device time (CUDA events on `stream`) of `fn()` after one warm-up call."""
+    out = fn()
+    ms = []
+    for _ in range(reps):
+        if flush is not None:
+            with torch.cuda.stream(stream):
+                flush.fill_(3)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = fn()
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    return out, ms
 
 
 def extras(pgm, torch, stream, flush):
     out = {}
-    # 4-motif counting on the Chung-Lu graph
+    # triangles on the Erdos-Renyi graph (launch-latency bound)
+    g = gg.triangle_er()
+    gold = load_json(os.path.join(GOLD, "triangle_er.json"))
+    with pgm.Graph(g, stream=stream) as G:
+        G.orient()
+        t, ms = timed_calls(lambda: G.kcliques(3), stream, torch, flush, reps=20)
+    out["triangles_er4096"] = {"count": t, "us_per_call": float(np.median(ms)) * 1e3,
+                               "exact_vs_oracle": (gold["clique_levels_k7"][3] == t) if gold else None}
+    # 5-cliques on R-MAT 21
+    g = gg.rmat21()
+    gold = load_json(os.path.join(GOLD, "rmat21_k5.json"))
+    pgm.pgm_set_options(profile=1)
+    with pgm.Graph(g, stream=stream) as G:
+        G.orient()
+        c5, ms = timed_calls(lambda: G.kcliques(5), stream, torch, flush, reps=2)
+        lv = [int(x) for x in pgm.pgm_last_profile()["level_size"][:6]]
+    pgm.pgm_set_options(profile=0)
+    t = float(np.mean(ms))
+    out["clique5_rmat21"] = {"count": c5, "ms_per_call": t, "embeddings_per_s": sum(lv[2:6]) / (t * 1e-3),
+                             "level_sizes": lv[1:],
+                             "exact_vs_oracle": (gold["clique_levels_k5"][2:] == lv[2:6]) if gold else None}
+    # 3- and 4-motifs on the Chung-Lu graph
     g = gg.chung_lu_1m()
     gold = load_json(os.path.join(GOLD, "chung_lu_1m.json"))
     pgm.pgm_set_options(profile=1)
@@ -382,6 +543,7 @@ def extras(pgm, torch, stream, flush):
         G.motifs(4)  # first call: also builds the degree-relabelled copy and the motif helpers
         torch.cuda.synchronize()
         t_first = (time.perf_counter() - t_first) * 1e3
+        m3, ms3 = timed_calls(lambda: G.motifs(3), stream, torch, flush, reps=5)
         ms, dom_ms, dom_b = [], 0.0, 0.0
         for _ in range(2):
             with torch.cuda.stream(stream):
@@ -401,6 +563,8 @@ def extras(pgm, torch, stream, flush):
         emb = sum(p["level_size"][2:5])
     pgm.pgm_set_options(profile=0)
     t = float(np.mean(ms))
+    out["motif3_chung_lu_1m"] = {"counts": m3, "ms_per_call": float(np.median(ms3)),
+                                 "exact_vs_oracle": (gold["motif3"] == m3) if gold else None}
     out["motif4_chung_lu_1m"] = {
         "value": emb / (t * 1e-3), "unit": "embeddings/s", "ms_per_step": t, "counts": m4,
         "exact_vs_oracle": (gold["motif4"] == m4) if gold else None, "embeddings_per_step": emb,
@@ -552,6 +716,50 @@ def serving(pgm, rate=2000.0, seconds=10.0, inflight=8, budget=60 << 30):
                 "wrong_or_failed": int(wrong), "max_inflight": inflight, "budget_bytes": budget}
     finally:
         pgm.pgm_server_destroy(s)
+
+
+def sweep(args):
+    """Weak-scaling series of the paper's R-MAT experiment (Sec. 6.4): scales
+    20.. at average degree 20 on one GPU.  Per scale: 3- and 4-clique counts
+    with the default (bitset) engine, timed with CUDA events, and the
+    level-list engine's counts beside them; levels are compared with the
+    oracle's stored counts where they exist (tests/golden/rmat_weak<s>.json)
+    and between the two engines everywhere.  One JSON line per scale."""
+    import torch
+
+    from paper_1911_06969_b300 import pgm
+
+    stream = torch.cuda.Stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    for s in [int(x) for x in args.sweep_scales.split(",") if x]:
+        t0 = time.perf_counter()
+        g = gg.rmat_weak(s)
+        gen_s = time.perf_counter() - t0
+        gold = load_json(os.path.join(GOLD, f"rmat_weak{s}.json"))
+        row = {"scale": s, "n": g.n, "m": g.m, "generate_s": round(gen_s, 1)}
+        try:
+            with pgm.Graph(g, stream=stream) as G:
+                G.orient()
+                for k in (3, 4):
+                    pgm.pgm_set_options(profile=1, clique_engine=0)
+                    c, ms = timed_calls(lambda: G.kcliques(k), stream, torch, flush, reps=3)
+                    lv = [int(x) for x in pgm.pgm_last_profile()["level_size"][:k + 1]]
+                    pgm.pgm_set_options(profile=0, clique_engine=1)
+                    c1, ms1 = timed_calls(lambda: G.kcliques(k), stream, torch, flush, reps=1)
+                    pgm.pgm_set_options(profile=0, clique_engine=0)
+                    t = float(np.median(ms))
+                    row[f"k{k}"] = {"count": c, "ms": round(t, 3), "embeddings_per_s": sum(lv[2:]) / (t * 1e-3),
+                                    "level_sizes": lv[1:], "level_list_ms": round(ms1[-1], 3),
+                                    "engines_agree": c == c1,
+                                    "exact_vs_oracle": (gold["clique_levels_k4"][2:k + 1] == lv[2:]) if gold else None}
+                m3, ms3 = timed_calls(lambda: G.motifs(3), stream, torch, flush, reps=3)
+                row["motif3"] = {"counts": m3, "ms": round(float(np.median(ms3)), 3),
+                                 "exact_vs_oracle": (gold["motif3"] == m3) if gold else None}
+        except Exception as e:  # noqa: BLE001 -- a scale that does not fit is reported, the series goes on
+            row["error"] = str(e)[:300]
+        print(json.dumps(row), flush=True)
+        del g
+    return 0
 
 
 if __name__ == "__main__":

@@ -312,3 +312,9 @@ def small_batch_20k(seed: int = 1) -> Batch:
 def serving_64(seed: int = 1) -> Batch:
     """64 resident graphs (32 R-MAT, 32 BA), n log-uniform in [1e3, 1e6], degree 8-32."""
     return _cached(f"serve64_s{seed}", lambda: batch_mixed(64, seed=seed))
+
+
+def rmat_weak(scale: int, seed: int = 1) -> CSR:
+    """R-MAT of the weak-scaling series: 2^scale vertices, average degree 20
+    (10 * 2^scale undirected edges), same (a, b, c, d) as the R-MAT workload."""
+    return _cached(f"rmat{scale}_d20_s{seed}", lambda: rmat(1 << scale, 10 << scale, RMAT_ABC, seed))

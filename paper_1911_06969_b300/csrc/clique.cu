@@ -435,9 +435,12 @@ pgm_status count_kcliques(Graph& g, Workspace& ws, cudaStream_t s, int k, int32_
         PGM_TRY(prof.finish(&lp));
         for (int i = 0; i < lp.nphases; i++) {
           pgm_phase& p = lp.phase[i];
-          // out-lists of the vertex and of each out-neighbour (4 B per element) + row pointers
+          // level 2 -> 3 of the extension: every level-2 embedding (DAG arc u -> v)
+          // reads the out-list of its last vertex v (4 B per element) and its own
+          // record (8 B), and every level-3 embedding is written (8 B) unless the
+          // last level is fused (k = 3).  Deeper levels are ANDs of on-chip rows.
           if (!strcmp(p.name, "bitset_count"))
-            p.alg_bytes = 4.0 * (double)ls[kBmLevelRead] + 4.0 * p.entries + 8.0 * (double)(v_hi - v_lo);
+            p.alg_bytes = 4.0 * (double)ls[kBmLevelRead] + 8.0 * (double)arcs + (k > 3 ? 8.0 * (double)ls[3] : 0.0);
         }
       }
       lp.level_size[1] = (uint64_t)(v_hi - v_lo);

@@ -4,7 +4,8 @@ Calls only the CPU oracle (``oracle/``) and the input generators
 (``graphgen/``); no value here comes from the CUDA library.  Run from the
 repository root:
 
-    python tests/golden/make_golden.py [triangle_er chung_lu_1m small_batch_20k serving_64 rmat21 rmat21_k5]
+    python tests/golden/make_golden.py [triangle_er chung_lu_1m small_batch_20k serving_64 rmat21 rmat21_k5
+                                        rmat_weak20 rmat_weak21 rmat_weak22]
 
 Each workload writes ``tests/golden/<name>.json``.
 """
@@ -116,6 +117,31 @@ def do_serving_64():
          "graph_sha256": graph_digest(b.graph), "G": b.G, "graphs": rows,
          "oracle_seconds": round(time.time() - t, 1)}
     write("serving_64", d)
+
+
+def _rmat_weak(scale):
+    g = gg.rmat_weak(scale)
+    t = time.time()
+    lv = oracle.clique_levels(g, 4, "degree", threads=THREADS)
+    d = {"workload": f"R-MAT scale {scale}, (a,b,c,d)=(0.57,0.19,0.19,0.05), average degree 20 "
+                     f"({10 << scale:,} edges), seed 1",
+         "graph_sha256": graph_digest(g), **stats(g), "clique_levels_k4": lv,
+         "motif3": oracle.formula_motifs(g, 3, threads=THREADS),
+         "oracle": "orc_clique_count, (degree, ID) order; orc_formula_motifs", "oracle_threads": THREADS,
+         "oracle_seconds": round(time.time() - t, 1)}
+    write(f"rmat_weak{scale}", d)
+
+
+def do_rmat_weak20():
+    _rmat_weak(20)
+
+
+def do_rmat_weak21():
+    _rmat_weak(21)
+
+
+def do_rmat_weak22():
+    _rmat_weak(22)
 
 
 if __name__ == "__main__":
