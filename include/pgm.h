@@ -87,7 +87,15 @@ typedef struct {
   int32_t motif_order;           /* full-range motif counts: 0 = on a copy relabelled by degree
                                     (ascending for k = 3, descending for k = 4; counts are unchanged),
                                     1 = on the input IDs (every call sets this field)              */
-  int32_t reserved[2];
+  int32_t count_headroom_log2;   /* test hook for PGM_EOVERFLOW, 0 = off (every call sets this field):
+                                    with x in [1, 63], the count accumulators of pgm_count_kcliques(_range)
+                                    and pgm_count_motifs(_range) start at 2^64 - 2^x and that start is
+                                    subtracted again on readback, so a count below 2^x is returned
+                                    unchanged and a count of 2^x or more fails with PGM_EOVERFLOW    */
+  int32_t motif_b_side_min;      /* 4-motif last level: a level-2 edge (v0, v1) with at least this many
+                                    children adjacent to v0 finds their common neighbours with v1 by
+                                    extending the members of N(v1) (one scan per edge), fewer scan each
+                                    child's own list (default 32; 1 = always, 2^30 = never)          */
 } pgm_options;
 
 /* Per-call profile (when options.profile = 1): one record per kernel phase. */
@@ -255,7 +263,9 @@ typedef struct {
   int32_t hub_threshold;  /* block-per-parent threshold           */
   int32_t blocks_per_sm;  /* persistent grid size per SM          */
   int32_t use_graph;      /* 1 = replay a captured CUDA graph     */
-  int32_t reserved[3];
+  int32_t motif_b_side_min;     /* intersection variant of the 4-motif last level (options field) */
+  int32_t reverse_ratio;        /* level-list intersection direction (options field)              */
+  int32_t bitset_forward_ratio; /* bitset row-building direction (options field)                  */
 } pgm_tune;
 
 /* Per-graph motif counts of every graph of the batch in one pass of the
@@ -277,6 +287,28 @@ pgm_status pgm_batch_count_motifs_loop(pgm_batch *b, int32_t k, uint64_t *out);
  * (exact counts are identical for every setting; a mismatch is reported
  * as PGM_EINVAL). */
 pgm_status pgm_batch_autotune(pgm_batch *b, int32_t k, pgm_tune *best, double *best_ms);
+
+/* One timed candidate of pgm_batch_autotune_ex. */
+typedef struct {
+  pgm_tune tune;
+  double ms; /* mean CUDA-event time of two timed runs after a warm-up */
+} pgm_tune_trial;
+
+/* pgm_batch_autotune (k = 3, 4) with its trials and a cache.  The search
+ * walks the knobs one at a time from the defaults -- block_threads {128,
+ * 256, 512}, warp_stage_cap {128, 256, 512, 1024}, blocks_per_sm {0, 2, 4},
+ * motif_b_side_min {8, 32, 128, 2^30} -- keeping each knob's fastest value.
+ *   trials, cap   every timed candidate in order, up to cap (NULL, 0: none);
+ *                 *n_trials receives the number written (may be NULL)
+ *   cache_path    a JSON file of earlier winners keyed by k and the batch's
+ *                 features (graphs, vertices, arcs, largest degree, each
+ *                 rounded down to a power of two), or NULL.  A hit returns
+ *                 the stored setting and time without timing anything
+ *                 (*from_cache = 1); a miss searches and adds the winner.
+ * Not safe against concurrent writers of the same cache file. */
+pgm_status pgm_batch_autotune_ex(pgm_batch *b, int32_t k, const char *cache_path, pgm_tune *best,
+                                 double *best_ms, pgm_tune_trial *trials, int32_t cap, int32_t *n_trials,
+                                 int32_t *from_cache);
 
 int32_t pgm_batch_size(const pgm_batch *b);
 void pgm_batch_destroy(pgm_batch *b);
@@ -363,6 +395,13 @@ const char *pgm_version(void);
 /* Number of CUDA kernels this library has launched in the process (all
  * threads; a CUDA-graph replay adds the kernel nodes of the graph). */
 uint64_t pgm_kernel_launches(void);
+
+/* Bounds-checked build (libpgm_debug.so, compiled with PGM_DEBUG): the
+ * number of out-of-range indices met at the checked global-memory sites
+ * since the last reset (each such access is skipped, nothing traps); when
+ * non-zero, pgm_last_error() names the first site and index.  reset != 0
+ * clears the counters.  Always 0 in the regular build. */
+uint64_t pgm_debug_errors(int32_t reset);
 
 #ifdef __cplusplus
 }

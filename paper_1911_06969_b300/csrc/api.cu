@@ -29,9 +29,23 @@ const char* get_error() { return t_err.c_str(); }
 static std::atomic<uint64_t> g_launches{0};
 void note_launches(uint64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
-static pgm_options g_opts = {256, 512, 0, 0, (int64_t)1 << 31, 0, 2, 0, 4, 1024, 0, {0}};
+static pgm_options g_opts = {256, 512, 0, 0, (int64_t)1 << 31, 0, 2, 0, 4, 1024, 0, 0, 32};
 
 pgm_options& options() { return g_opts; }
+
+unsigned long long count_seed() {
+  const int x = g_opts.count_headroom_log2;
+  return (x > 0 && x < 64) ? 0ull - (1ull << x) : 0ull;
+}
+
+pgm_status seed_counts(unsigned long long* dev, int n, cudaStream_t s) {
+  const unsigned long long seed = count_seed();
+  if (!seed || current_plan()) return PGM_OK;
+  std::vector<unsigned long long> h((size_t)n, seed);
+  PGM_TRY_CUDA(cudaMemcpyAsync(dev, h.data(), (size_t)n * sizeof(unsigned long long), cudaMemcpyHostToDevice, s));
+  PGM_TRY_CUDA(cudaStreamSynchronize(s));
+  return PGM_OK;
+}
 
 int device_id() {
   int d = 0;
@@ -215,8 +229,53 @@ void Workspace::release_all() {
 
 }  // namespace pgm
 
+#ifdef PGM_DEBUG
+namespace pgm {
+namespace {
+struct DebugReg {
+  const char* file;
+  cudaError_t (*read)(DebugWord*);
+  cudaError_t (*reset)();
+};
+std::vector<DebugReg>& debug_regs() {
+  static std::vector<DebugReg> v;
+  return v;
+}
+}  // namespace
+int register_debug_word(const char* file, cudaError_t (*read)(DebugWord*), cudaError_t (*reset)()) {
+  debug_regs().push_back({file, read, reset});
+  return (int)debug_regs().size();
+}
+}  // namespace pgm
+#endif
+
 // ------------------------------------------------------------------- C ABI
 extern "C" {
+
+uint64_t pgm_debug_errors(int32_t reset) {
+#ifdef PGM_DEBUG
+  uint64_t total = 0;
+  bool first = true;
+  for (const auto& r : pgm::debug_regs()) {
+    pgm::DebugWord w = {0, 0, 0};
+    if (r.read(&w) != cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
+    if (w.count && first) {
+      pgm::set_error("out-of-range index %lld at %s:%llu (%llu violations in that file)", (long long)w.index,
+                     r.file, w.line, w.count);
+      first = false;
+    }
+    total += w.count;
+    if (reset && r.reset() != cudaSuccess) cudaGetLastError();
+  }
+  return total;
+#else
+  (void)reset;
+  return 0;
+#endif
+}
 
 const char* pgm_last_error(void) { return pgm::get_error(); }
 
@@ -297,6 +356,18 @@ pgm_status pgm_set_options(const pgm_options* o) {
     return PGM_EINVAL;
   }
   next.motif_order = v.motif_order;
+  if (v.count_headroom_log2 < 0 || v.count_headroom_log2 > 63) {
+    pgm::set_error("count_headroom_log2 must be 0 (off) or in [1, 63]");
+    return PGM_EINVAL;
+  }
+  next.count_headroom_log2 = v.count_headroom_log2;
+  if (v.motif_b_side_min) {
+    if (v.motif_b_side_min < 1) {
+      pgm::set_error("motif_b_side_min must be >= 1");
+      return PGM_EINVAL;
+    }
+    next.motif_b_side_min = v.motif_b_side_min;
+  }
   next.profile = v.profile ? 1 : 0;
   pgm::options() = next;
   return PGM_OK;

@@ -21,7 +21,11 @@
 // vertex range) in a host loop, with its natural per-level syncs.
 #include <algorithm>
 #include <chrono>
+#include <cstdio>
 #include <cstring>
+#include <string>
+#include <utility>
+#include <vector>
 #include <memory>
 #include <new>
 
@@ -94,6 +98,9 @@ struct TuneScope {
     if (t->warp_stage_cap) o.warp_stage_cap = t->warp_stage_cap;
     if (t->hub_threshold) o.hub_threshold = t->hub_threshold;
     if (t->blocks_per_sm) o.blocks_per_sm = t->blocks_per_sm;
+    if (t->motif_b_side_min) o.motif_b_side_min = t->motif_b_side_min;
+    if (t->reverse_ratio) o.reverse_ratio = t->reverse_ratio;
+    if (t->bitset_forward_ratio) o.bitset_forward_ratio = t->bitset_forward_ratio;
   }
   ~TuneScope() { options() = saved; }
 };
@@ -138,7 +145,9 @@ pgm_status engine(pgm_batch* b, Workspace& ws, int kind, int k, unsigned long lo
 
 bool same_tune(const pgm_tune& a, const pgm_tune& c) {
   return a.block_threads == c.block_threads && a.warp_stage_cap == c.warp_stage_cap &&
-         a.hub_threshold == c.hub_threshold && a.blocks_per_sm == c.blocks_per_sm;
+         a.hub_threshold == c.hub_threshold && a.blocks_per_sm == c.blocks_per_sm &&
+         a.motif_b_side_min == c.motif_b_side_min && a.reverse_ratio == c.reverse_ratio &&
+         a.bitset_forward_ratio == c.bitset_forward_ratio;
 }
 
 // counters block layout shared with the engines: error slots to inspect
@@ -147,6 +156,10 @@ pgm_status check_err_slots(const unsigned long long* h, int kind) {
   if (e) {
     set_error("batch: internal hub-list overflow");
     return PGM_ENOMEM;
+  }
+  if (h[kCarrySlot]) {
+    set_error("batch: a count exceeds 2^64 - 1");
+    return PGM_EOVERFLOW;
   }
   return PGM_OK;
 }
@@ -262,6 +275,111 @@ pgm_status run_batch(pgm_batch* b, int kind, int k, uint64_t* out, const pgm_tun
   PGM_TRY_CUDA(cudaStreamSynchronize(s));
   PGM_TRY(check_err_slots(b->pinned_ctr, kind));
   memcpy(out, b->pinned_pg, pg_bytes);
+  return PGM_OK;
+}
+
+// --------------------------------------------------------- autotune cache
+// Winners of pgm_batch_autotune_ex kept in a small JSON object, one entry
+// per line: "<key>": {"block_threads": .., "warp_stage_cap": ..,
+// "hub_threshold": .., "blocks_per_sm": .., "motif_b_side_min": ..,
+// "reverse_ratio": .., "bitset_forward_ratio": .., "ms": ..}.  The key holds
+// the motif size and the batch's features rounded down to powers of two:
+// graphs, vertices, arcs and largest degree.
+int ilog2(int64_t x) {
+  int l = 0;
+  while (x > 1) {
+    x >>= 1;
+    l++;
+  }
+  return l;
+}
+
+std::string tune_key(pgm_batch* b, int k) {
+  char buf[128];
+  snprintf(buf, sizeof(buf), "motif%d_G2^%d_n2^%d_arcs2^%d_dmax2^%d", k, ilog2(b->G), ilog2(b->g.n),
+           ilog2(b->g.narcs), ilog2(b->g.dmax));
+  return buf;
+}
+
+// every "key": {...} line of the file (an absent or unreadable file is empty)
+std::vector<std::pair<std::string, std::string>> tune_cache_read(const char* path) {
+  std::vector<std::pair<std::string, std::string>> out;
+  FILE* f = fopen(path, "r");
+  if (!f) return out;
+  char line[1024];
+  while (fgets(line, sizeof(line), f)) {
+    const char* q0 = strchr(line, '"');
+    const char* q1 = q0 ? strchr(q0 + 1, '"') : nullptr;
+    const char* b0 = q1 ? strchr(q1, '{') : nullptr;
+    const char* b1 = b0 ? strchr(b0, '}') : nullptr;
+    if (!b1) continue;
+    out.emplace_back(std::string(q0 + 1, q1), std::string(b0, b1 + 1));
+  }
+  fclose(f);
+  return out;
+}
+
+bool json_field(const std::string& body, const char* name, double* v) {
+  const std::string pat = std::string("\"") + name + "\":";
+  const size_t i = body.find(pat);
+  if (i == std::string::npos) return false;
+  return sscanf(body.c_str() + i + pat.size(), "%lf", v) == 1;
+}
+
+bool tune_cache_get(const char* path, const std::string& key, pgm_tune* t, double* ms) {
+  for (const auto& e : tune_cache_read(path)) {
+    if (e.first != key) continue;
+    double v[8];
+    static const char* names[8] = {"block_threads", "warp_stage_cap", "hub_threshold", "blocks_per_sm",
+                                   "motif_b_side_min", "reverse_ratio", "bitset_forward_ratio", "ms"};
+    for (int i = 0; i < 8; i++)
+      if (!json_field(e.second, names[i], &v[i])) return false;
+    memset(t, 0, sizeof(*t));
+    t->block_threads = (int32_t)v[0];
+    t->warp_stage_cap = (int32_t)v[1];
+    t->hub_threshold = (int32_t)v[2];
+    t->blocks_per_sm = (int32_t)v[3];
+    t->motif_b_side_min = (int32_t)v[4];
+    t->reverse_ratio = (int32_t)v[5];
+    t->bitset_forward_ratio = (int32_t)v[6];
+    t->use_graph = 1;
+    *ms = v[7];
+    return check_tune(t) == PGM_OK;
+  }
+  return false;
+}
+
+pgm_status tune_cache_put(const char* path, const std::string& key, const pgm_tune& t, double ms) {
+  auto entries = tune_cache_read(path);
+  char body[512];
+  snprintf(body, sizeof(body),
+           "{\"block_threads\": %d, \"warp_stage_cap\": %d, \"hub_threshold\": %d, \"blocks_per_sm\": %d, "
+           "\"motif_b_side_min\": %d, \"reverse_ratio\": %d, \"bitset_forward_ratio\": %d, \"ms\": %.3f}",
+           t.block_threads, t.warp_stage_cap, t.hub_threshold, t.blocks_per_sm, t.motif_b_side_min,
+           t.reverse_ratio, t.bitset_forward_ratio, ms);
+  bool found = false;
+  for (auto& e : entries)
+    if (e.first == key) {
+      e.second = body;
+      found = true;
+    }
+  if (!found) entries.emplace_back(key, body);
+  const std::string tmp = std::string(path) + ".tmp";
+  FILE* f = fopen(tmp.c_str(), "w");
+  if (!f) {
+    set_error("autotune cache: cannot write %s", tmp.c_str());
+    return PGM_EINVAL;
+  }
+  fprintf(f, "{\n");
+  for (size_t i = 0; i < entries.size(); i++)
+    fprintf(f, " \"%s\": %s%s\n", entries[i].first.c_str(), entries[i].second.c_str(),
+            i + 1 < entries.size() ? "," : "");
+  fprintf(f, "}\n");
+  fclose(f);
+  if (rename(tmp.c_str(), path) != 0) {
+    set_error("autotune cache: cannot replace %s", path);
+    return PGM_EINVAL;
+  }
   return PGM_OK;
 }
 
@@ -411,70 +529,117 @@ pgm_status pgm_batch_count_motifs_loop(pgm_batch* b, int32_t k, uint64_t* out) {
 }
 
 pgm_status pgm_batch_autotune(pgm_batch* b, int32_t k, pgm_tune* best, double* best_ms) {
-  if (!b || !best || !best_ms) {
-    pgm::set_error("pgm_batch_autotune: null argument");
+  return pgm_batch_autotune_ex(b, k, nullptr, best, best_ms, nullptr, 0, nullptr, nullptr);
+}
+
+pgm_status pgm_batch_autotune_ex(pgm_batch* b, int32_t k, const char* cache_path, pgm_tune* best, double* best_ms,
+                                 pgm_tune_trial* trials, int32_t cap, int32_t* n_trials, int32_t* from_cache) {
+  if (!b || !best || !best_ms || cap < 0 || (cap > 0 && !trials)) {
+    pgm::set_error("pgm_batch_autotune: bad arguments");
     return PGM_EINVAL;
   }
   if (k != 3 && k != 4) {
     pgm::set_error("pgm_batch_autotune: k=%d unsupported", k);
     return PGM_EUNSUPPORTED;
   }
-  // candidate schedules: block size, per-warp staging capacity, hub
-  // threshold (warp -> block kernel), persistent blocks per SM
-  static const int cand[][4] = {{256, 512, 512, 0},  {256, 256, 256, 0},  {256, 1024, 1024, 0},
-                                {128, 512, 512, 0},  {512, 512, 512, 0},  {256, 512, 128, 0},
-                                {256, 128, 128, 0},  {256, 512, 512, 2},  {128, 256, 256, 0},
-                                {256, 2048, 2048, 0}};
+  if (n_trials) *n_trials = 0;
+  if (from_cache) *from_cache = 0;
+  const std::string key = pgm::tune_key(b, k);
+  if (cache_path) {
+    pgm_tune t;
+    double ms = 0;
+    if (pgm::tune_cache_get(cache_path, key, &t, &ms)) {
+      *best = t;
+      *best_ms = ms;
+      if (from_cache) *from_cache = 1;
+      return PGM_OK;
+    }
+  }
+  // coordinate descent over the knobs of the motif engine, from the
+  // defaults: block size, staging capacity, persistent blocks per SM, and
+  // the intersection variant of the last level (B-side threshold); each
+  // knob's values are timed with the others at their best so far
   const int np = k == 3 ? 2 : 6;
   std::vector<uint64_t> ref((size_t)std::max(b->G, 1) * np), got(ref.size());
   cudaStream_t s = b->g.stream;
   cudaEvent_t e0, e1;
   PGM_TRY_CUDA(cudaEventCreate(&e0));
   PGM_TRY_CUDA(cudaEventCreate(&e1));
+  pgm_tune cur;
+  memset(&cur, 0, sizeof(cur));
+  cur.block_threads = 256;
+  cur.warp_stage_cap = 512;
+  cur.motif_b_side_min = 32;
   double bms = 1e30;
-  pgm_tune bt;
-  memset(&bt, 0, sizeof(bt));
-  pgm_status st = PGM_OK;
   bool have_ref = false;
-  for (const auto& c : cand) {
-    pgm_tune t;
-    memset(&t, 0, sizeof(t));
-    t.block_threads = c[0];
-    t.warp_stage_cap = c[1];
-    t.hub_threshold = c[2];
-    t.blocks_per_sm = c[3];
-    st = pgm::run_batch(b, pgm::kMotif, k, got.data(), &t);  // warm-up + exactness check
-    if (st != PGM_OK) break;
+  int nt = 0;
+  std::vector<pgm_tune> tried;
+  auto time_one = [&](const pgm_tune& t, double* out_ms) -> pgm_status {
+    PGM_TRY(pgm::run_batch(b, pgm::kMotif, k, got.data(), &t));  // warm-up + exactness check
     if (!have_ref) {
       ref = got;
       have_ref = true;
     } else if (got != ref) {
       pgm::set_error("pgm_batch_autotune: counts differ between schedules");
-      st = PGM_EINVAL;
-      break;
+      return PGM_EINVAL;
     }
     double tot = 0;
-    for (int rep = 0; rep < 2 && st == PGM_OK; rep++) {
+    for (int rep = 0; rep < 2; rep++) {
       cudaEventRecord(e0, s);
-      st = pgm::run_batch(b, pgm::kMotif, k, got.data(), &t);
+      PGM_TRY(pgm::run_batch(b, pgm::kMotif, k, got.data(), &t));
       cudaEventRecord(e1, s);
       cudaEventSynchronize(e1);
       float ms = 0;
       cudaEventElapsedTime(&ms, e0, e1);
       tot += ms;
     }
-    if (st != PGM_OK) break;
-    if (tot / 2 < bms) {
-      bms = tot / 2;
-      bt = t;
+    *out_ms = tot / 2;
+    return PGM_OK;
+  };
+  static const int kThreads[] = {128, 256, 512};
+  static const int kCaps[] = {128, 256, 512, 1024};
+  static const int kPerSM[] = {0, 2, 4};
+  static const int kBSide[] = {8, 32, 128, 1 << 30};
+  pgm_status st = PGM_OK;
+  for (int knob = 0; knob < 4 && st == PGM_OK; knob++) {
+    const int* vals = knob == 0 ? kThreads : knob == 1 ? kCaps : knob == 2 ? kPerSM : kBSide;
+    const int nv = knob == 0 ? 3 : knob == 2 ? 3 : 4;
+    pgm_tune base = cur;
+    for (int i = 0; i < nv && st == PGM_OK; i++) {
+      pgm_tune t = base;
+      int* f = knob == 0 ? &t.block_threads : knob == 1 ? &t.warp_stage_cap : knob == 2 ? &t.blocks_per_sm
+                                                                                       : &t.motif_b_side_min;
+      *f = vals[i];
+      if ((t.block_threads / 32) * t.warp_stage_cap > 16384) continue;  // shared memory of the warp kernels
+      bool seen = false;
+      for (const auto& u : tried) seen = seen || (u.block_threads == t.block_threads &&
+                                                  u.warp_stage_cap == t.warp_stage_cap &&
+                                                  u.blocks_per_sm == t.blocks_per_sm &&
+                                                  u.motif_b_side_min == t.motif_b_side_min);
+      if (seen) continue;
+      tried.push_back(t);
+      double ms = 0;
+      st = time_one(t, &ms);
+      if (st != PGM_OK) break;
+      if (nt < cap) {
+        trials[nt].tune = t;
+        trials[nt].ms = ms;
+      }
+      nt++;
+      if (ms < bms) {
+        bms = ms;
+        cur = t;
+      }
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (st != PGM_OK) return st;
-  bt.use_graph = 1;
-  *best = bt;
+  cur.use_graph = 1;
+  *best = cur;
   *best_ms = bms;
+  if (n_trials) *n_trials = std::min(nt, cap);
+  if (cache_path) PGM_TRY(pgm::tune_cache_put(cache_path, key, cur, bms));
   return PGM_OK;
 }
 

@@ -173,6 +173,7 @@ struct CliqueRun {
     A.stat = ctr() + kSlotStat + 3 * level + MODE;
     A.queue = ctr() + kSlotQueue;
     A.err = ctr() + kSlotErr;
+    A.carry = ctr() + kCarrySlot;
     A.big = ws.big.p;
     A.big_cap = big_cap;
     A.hub = hub_eff;
@@ -454,6 +455,7 @@ pgm_status count_kcliques(Graph& g, Workspace& ws, cudaStream_t s, int k, int32_
   PGM_TRY(graph_host_dag_rp(g));  // edge blocking plans on the host row pointers
   PGM_TRY(ws.ctr.reserve(kSlots));
   PGM_TRY_CUDA(cudaMemsetAsync(ws.ctr.p, 0, kSlots * sizeof(unsigned long long), s));
+  if (!per_graph_dev) PGM_TRY(seed_counts(ws.ctr.p + kSlotAcc, 1, s));
   CliqueRun run(g, ws, s, k);
   run.per_graph = per_graph_dev;
   Lvl L2;
@@ -476,6 +478,11 @@ pgm_status count_kcliques(Graph& g, Workspace& ws, cudaStream_t s, int k, int32_
     set_error("count_kcliques: internal hub-list overflow");
     return PGM_ENOMEM;
   }
+  if (h[kCarrySlot]) {
+    set_error("count_kcliques: the count exceeds 2^64 - 1");
+    return PGM_EOVERFLOW;
+  }
+  h[kSlotAcc] -= per_graph_dev ? 0ull : count_seed();
   *out = h[kSlotAcc];
   Profiler& prof = profiler();
   if (prof.on) {

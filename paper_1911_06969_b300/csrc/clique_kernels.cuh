@@ -37,18 +37,14 @@ struct LevelArgs {
   int rev_ratio;              // reverse scan when d+(w) > rev_ratio * |segment|
   const int32_t* gid;         // vertex -> graph (batches) or nullptr
   unsigned long long* per_graph;  // kSum with gid: per-graph counts
+  unsigned long long* carry;      // wraps of the count accumulators (add_count)
 };
 
 // Flush a per-lane count to the graph's counter (warp-wide reduction).
 __device__ __forceinline__ void flush_count(const LevelArgs& A, unsigned long long& tot, int g,
                                             int lane) {
   unsigned long long s = warp_sum(tot);
-  if (lane == 0 && s) {
-    if (A.per_graph && g >= 0)
-      atomicAdd(A.per_graph + g, s);
-    else
-      atomicAdd(A.acc, s);
-  }
+  if (lane == 0 && s) add_count((A.per_graph && g >= 0) ? A.per_graph + g : A.acc, s, false, A.carry);
   tot = 0;
 }
 

@@ -60,6 +60,7 @@ struct BmArgs {
   unsigned long long* per_graph;
   unsigned long long* deep;   // k >= 6: [t] entries of level t + 3 (t = 2 .. k - 4)
   int clevels;                // C buffers per warp: 1, or k - 4 for k >= 6
+  unsigned long long* carry;  // wraps of the count accumulators (add_count)
 };
 
 // bucket of a vertex with out-degree d > kBmWarpD
@@ -73,8 +74,8 @@ __device__ __forceinline__ void bm_flush(const BmArgs& B, unsigned long long (&c
   for (int i = 0; i < 3; i++) {
     unsigned long long s = warp_sum(c[i]);
     if (lane == 0 && s) {
-      if (i == 0 && B.per_graph && g >= 0)
-        atomicAdd(B.per_graph + g, s);
+      if (i == 0)
+        add_count((B.per_graph && g >= 0) ? B.per_graph + g : B.acc, s, false, B.carry);
       else
         atomicAdd(B.acc + i, s);
     }
@@ -595,7 +596,8 @@ __global__ void __launch_bounds__(THREADS, bm_min_blocks(DMAX, THREADS, KV)) bm_
       P = sP;
       R = sRows;
     } else {
-      for (int64_t i = threadIdx.x; i < (int64_t)d * S; i += THREADS) gRows[i] = 0;
+      for (int64_t i = threadIdx.x; i < (int64_t)d * S; i += THREADS)
+        if (PGM_IDX_OK(i, B.scratch_words)) gRows[i] = 0;
       P = B.col + a0;
       R = gRows;
     }
@@ -651,6 +653,7 @@ __global__ void __launch_bounds__(THREADS, bm_min_blocks(DMAX, THREADS, KV)) bm_
     // level 3 and beyond: one warp per row i
     // C buffers of the warp: R_i & R_j (5-cliques) or the chain's C_1 .. C_D (k >= 6)
     uint32_t* C = DMAX > 0 ? sC : gRows + (int64_t)d * S + (int64_t)wid * S * CL;
+    if (DMAX == 0 && lane == 0) PGM_IDX_OK((int64_t)d * S + (int64_t)(wid + 1) * S * CL - 1, B.scratch_words);
     const int64_t cstride = DMAX > 0 ? 4 * S4MAX : S;
     // row j (32-bit offsets when the rows are in shared memory)
     auto row4 = [&](int j) {
@@ -794,6 +797,8 @@ pgm_status count_kcliques_bitset(Graph& g, Workspace& ws, cudaStream_t s, int k,
   PGM_TRY(ws.big.reserve((size_t)(total + 1) / 2 + 1));
   if (words > 0) PGM_TRY(ws.vid[11].reserve((size_t)kern[3].grid * (size_t)words));
   PGM_TRY_CUDA(cudaMemsetAsync(ws.ctr.p, 0, kBmSlots * sizeof(unsigned long long), s));
+  if (!per_graph_dev) PGM_TRY(seed_counts(ws.ctr.p + 8, 1, s));
+  B.carry = ws.ctr.p + kCarrySlot;
   B.rp = g.dag_rp;
   B.col = g.dag_col;
   B.v_lo = v_lo;
@@ -839,7 +844,11 @@ pgm_status count_kcliques_bitset(Graph& g, Workspace& ws, cudaStream_t s, int k,
     set_error("bitset engine: internal big-vertex list overflow");
     return PGM_ENOMEM;
   }
-  *out = h[8];
+  if (h[kCarrySlot]) {
+    set_error("count_kcliques: the count exceeds 2^64 - 1");
+    return PGM_EOVERFLOW;
+  }
+  *out = h[8] - (per_graph_dev ? 0ull : count_seed());
   if (level_sizes) {  // [l] entries of level l (3 <= l < k), [kBmLevelRead] adjacency elements read
     level_sizes[3] = h[9];
     level_sizes[4] = h[10];

@@ -49,6 +49,13 @@ void note_launches(uint64_t n);
 
 // ----------------------------------------------------------------- options
 pgm_options& options();  // current options (defaults filled); read-only while counting
+// Start value of the count accumulators (options.count_headroom_log2: 2^64 -
+// 2^x, else 0) and the host write of it into n device slots (not while a
+// plan is replayed).  Readback subtracts count_seed() again.
+unsigned long long count_seed();
+// counter-block slot of every engine that accumulates add_count() wraps
+constexpr int kCarrySlot = 5;
+pgm_status seed_counts(unsigned long long* dev, int n, cudaStream_t s);
 int num_sms();            // SM count of the current device
 int device_id();
 
@@ -307,6 +314,39 @@ int grid_for(const void* fn, int threads, size_t smem);
 // raise a kernel's dynamic shared-memory limit once per process
 pgm_status smem_attr(const void* fn, int bytes);
 
+// -------------------------------------------------------- checked indexing
+// Builds with PGM_DEBUG check the index of every marked global access
+// against the length of its array (PGM_IDX_OK(i, n)): a violation adds one
+// to a device error word of the translation unit, the first one records its
+// source line and index, and the caller skips the access (a load yields a
+// neutral value).  Nothing traps.  Without PGM_DEBUG the check compiles to
+// `true`.  pgm_debug_errors() sums the words of all translation units.
+#ifdef PGM_DEBUG
+struct DebugWord {
+  unsigned long long count, line, index;
+};
+static __device__ DebugWord g_pgm_debug;
+__device__ __forceinline__ bool idx_ok(long long i, long long n, int line) {
+  if (i >= 0 && i < n) return true;
+  if (atomicAdd(&g_pgm_debug.count, 1ull) == 0ull) {
+    g_pgm_debug.line = (unsigned long long)line;
+    g_pgm_debug.index = (unsigned long long)i;
+  }
+  return false;
+}
+// host: register this translation unit's word (reader and reset) by name
+int register_debug_word(const char* file, cudaError_t (*read)(DebugWord*), cudaError_t (*reset)());
+static cudaError_t read_debug_word(DebugWord* out) { return cudaMemcpyFromSymbol(out, g_pgm_debug, sizeof(DebugWord)); }
+static cudaError_t reset_debug_word() {
+  DebugWord z = {0, 0, 0};
+  return cudaMemcpyToSymbol(g_pgm_debug, &z, sizeof(z));
+}
+static const int g_debug_registered = register_debug_word(__FILE__, read_debug_word, reset_debug_word);
+#else
+__device__ __forceinline__ bool idx_ok(long long, long long, int) { return true; }
+#endif
+#define PGM_IDX_OK(i, n) ::pgm::idx_ok((long long)(i), (long long)(n), __LINE__)
+
 // -------------------------------------------------------- device helpers
 constexpr unsigned kFull = 0xffffffffu;
 
@@ -350,6 +390,22 @@ __device__ __forceinline__ int warp_owner(int incl, int t) {
     if (v <= t) q += step;
   }
   return q;
+}
+
+// Adds one warp's partial count s to a uint64 accumulator and records a
+// wrap in *carry: +1 when the sum passes 2^64 - 1 upward, -1 (two's
+// complement) when a negative partial of a signed sum (sgn) passes 0
+// downward.  The accumulated total lies in [0, 2^64) exactly when *carry
+// ends at 0 (PGM_EOVERFLOW otherwise).
+__device__ __forceinline__ void add_count(unsigned long long* acc, unsigned long long s, bool sgn,
+                                          unsigned long long* carry) {
+  const unsigned long long old = atomicAdd(acc, s);
+  const unsigned long long now = old + s;
+  if (sgn && (long long)s < 0) {
+    if (now > old) atomicAdd(carry, ~0ull);
+  } else if (now < old) {
+    atomicAdd(carry, 1ull);
+  }
 }
 
 template <typename T>

@@ -89,6 +89,12 @@ struct MotifArgs {
   // written by the level-3 inspection, read by the last level (memoised
   // per level-2 edge, Sec. 4.2, instead of recomputed per level-3 entry)
   uint2* tri;
+  unsigned long long* carry;  // wraps of the count accumulators (add_count)
+  int b_side_min;  // last level: edges with at least this many f2 = 0 children find them from B's side
+  // lengths for the checked index sites (PGM_DEBUG builds)
+  int64_t narcs;        // col, rev, src
+  int64_t n_arc_slots;  // cnt, tri (arcs of the launch's vertex range)
+  int64_t n_l3;         // l3 entries of the chunk
 };
 
 template <int N>
@@ -99,7 +105,7 @@ __device__ __forceinline__ void flush_patterns(const MotifArgs& P, long long (&c
     long long s = warp_sum(c[i]);
     if (lane == 0 && s) {
       unsigned long long* dst = (P.per_graph && g >= 0) ? P.per_graph + (int64_t)g * N : P.acc;
-      atomicAdd(dst + i, (unsigned long long)s);
+      add_count(dst + i, (unsigned long long)s, true, P.carry);  // corrections make partials signed
     }
     c[i] = 0;
   }
@@ -147,7 +153,8 @@ __device__ __forceinline__ void l2_batch(const MotifArgs& P, const int32_t* A, i
       const int jq = j0 + q;
       if (jq >= s) break;
       const int64_t oq = __shfl_sync(kFull, my_off, q);
-      for (int i = jq + 1 + lane; i < s; i += 32) P.l3[oq + (i - jq - 1)] = (uint32_t)A[i] | kA02;
+      for (int i = jq + 1 + lane; i < s; i += 32)
+        if (PGM_IDX_OK(oq + (i - jq - 1), P.n_l3)) P.l3[oq + (i - jq - 1)] = (uint32_t)A[i] | kA02;
     }
     __syncwarp();
   }
@@ -186,9 +193,9 @@ __device__ __forceinline__ void l2_batch(const MotifArgs& P, const int32_t* A, i
         const int64_t oq = __shfl_sync(kFull, my_off, q);
         const int jq = j0 + q;
         const uint32_t rq = wcnt[q];
-        if (child)
-          P.l3[oq + (s - jq - 1) + rq + __popc(b & from_first & ((1u << lane) - 1u))] = (uint32_t)x | kA12;
-        if (tri) P.l3[oq + (xi - jq - 1)] = (uint32_t)x | kA02 | kA12;
+        const int64_t ic = oq + (s - jq - 1) + rq + __popc(b & from_first & ((1u << lane) - 1u));
+        if (child && PGM_IDX_OK(ic, P.n_l3)) P.l3[ic] = (uint32_t)x | kA12;
+        if (tri && PGM_IDX_OK(oq + (xi - jq - 1), P.n_l3)) P.l3[oq + (xi - jq - 1)] = (uint32_t)x | kA02 | kA12;
       }
       const int qn = __shfl_down_sync(kFull, q, 1);
       const bool last = active && (lane == 31 || t + 1 >= total || qn != q);
@@ -286,7 +293,7 @@ __device__ __forceinline__ void l2_count_batch(const MotifArgs& P, const int32_t
     }
   }
   if (MODE == mCount) {
-    if (valid) {
+    if (valid && PGM_IDX_OK(arc0 + j, P.n_arc_slots)) {
       P.cnt[arc0 + j] = (uint32_t)(s - j - 1) + (uint32_t)nbj - wcnt[lane];
       P.tri[arc0 + j] = make_uint2(wcnt[lane], wcnt[32 + lane]);
     }
@@ -484,6 +491,9 @@ __device__ __forceinline__ bool mf_test(const uint32_t* F, int shift, int32_t w)
   return ((F[h >> 5] >> (h & 31)) & 1u) != 0;
 }
 
+// arc (v0, v2) of the f2 = 0 child at position t0 of edge (v0, A[j1])
+__device__ __forceinline__ int64_t a2_of(int32_t u0, int j1, int t0) { return (int64_t)u0 + j1 + 1 + t0; }
+
 __device__ __forceinline__ bool row_bit(const uint32_t* row, int32_t w) {
   return ((row[w >> 5] >> (w & 31)) & 1u) != 0;
 }
@@ -506,8 +516,9 @@ __host__ __device__ constexpr int64_t ml3_warp_ints(int cap) {
 // | knowledge << 5) << 32), so the exact tests run on full warps.  The
 // loads of kU chunks of 32 slots are issued before their tests.
 template <int kU, class Test, class Hit>
-__device__ __forceinline__ void flat_scan(const int32_t* __restrict__ col, int len, int start, int tag0, int tag1,
-                                          unsigned long long* Qe, int32_t* Qs, int lane, Test test, Hit hit) {
+__device__ __forceinline__ void flat_scan(const int32_t* __restrict__ col, int64_t ncol, int len, int start, int tag0,
+                                          int tag1, unsigned long long* Qe, int32_t* Qs, int lane, Test test,
+                                          Hit hit) {
   const unsigned lt = (1u << lane) - 1u;
   const unsigned nem = __ballot_sync(kFull, len > 0);
   if (!nem) return;
@@ -545,7 +556,7 @@ __device__ __forceinline__ void flat_scan(const int32_t* __restrict__ col, int l
       q0 += __popc(S);
       const int t = b + lane;
       const int oq = __shfl_sync(kFull, coff, q);
-      wv[r] = t < total ? col[oq + t] : -1;
+      wv[r] = (t < total && PGM_IDX_OK(oq + t, ncol)) ? col[oq + t] : -1;
       qv[r] = q;
     }
 #pragma unroll
@@ -601,7 +612,6 @@ __device__ __forceinline__ void flat_scan(const int32_t* __restrict__ col, int l
 // events and folded into the six pattern counters once per edge.
 constexpr int kML3Threads = 256;  // block size of the last level (at most)
 constexpr int kML3Cap = 256;      // staging capacity (ints per list per warp) of the last level
-constexpr int kFromB = 32;        // edges with at least this many f2 = 0 children find them from B's side
 
 __global__ void __launch_bounds__(kML3Threads, 3) motif_l3_edge(MotifArgs P) {
   extern __shared__ __align__(16) int32_t smem[];
@@ -674,7 +684,7 @@ __global__ void __launch_bounds__(kML3Threads, 3) motif_l3_edge(MotifArgs P) {
       const int fwB = mf_words(nb, 8), shB = mf_shift(fwB);
       __syncwarp();
       if (!hArow && restage) mf_build(FA, fwA, shA, A, s, lane);
-      if (!hBrow && (f1any || nf0 < kFromB)) mf_build(FB, fwB, shB, B, nb, lane);
+      if (!hBrow && (f1any || nf0 < P.b_side_min)) mf_build(FB, fwB, shB, B, nb, lane);
       // I = A & B, sorted: scan the shorter list, test membership in the other
       int32_t* I = min(s, nb) <= P.cap ? Ismem : Iglob;
       int ni = 0;
@@ -693,7 +703,8 @@ __global__ void __launch_bounds__(kML3Threads, 3) motif_l3_edge(MotifArgs P) {
             in = member(Y, ny, hy, P, x);
           }
           const unsigned bal = __ballot_sync(kFull, in);
-          if (in) I[ni + __popc(bal & lt)] = x;
+          if (in && PGM_IDX_OK(ni + __popc(bal & lt), I == Ismem ? P.cap : P.scratch_stride))
+            I[ni + __popc(bal & lt)] = x;
           ni += __popc(bal);
         }
       }
@@ -705,7 +716,7 @@ __global__ void __launch_bounds__(kML3Threads, 3) motif_l3_edge(MotifArgs P) {
       int y1a = 0, y1b = 0, y2a = 0, y2b = 0, eh = 0, er = 0;
       // Children scans, N(v2) & (v0, inf), 32 lists at a time (tags: v2,
       // f2 = 0 | a12 << 1): always for f2 = 1 children, and for the f2 = 0
-      // children of edges with fewer than kFromB of them (the others' common
+      // children of edges with fewer than b_side_min of them (the others' common
       // neighbours are found from B's side by motif_l3_pairs).  Candidates:
       // f2 = 0 children, in B; f2 = 1 children, in A or B (not v1).
       // Knowledge bits: A known, in A, B known, in B.
@@ -738,20 +749,20 @@ __global__ void __launch_bounds__(kML3Threads, 3) motif_l3_edge(MotifArgs P) {
           er += ib && !ia && x > t0;
         }
       };
-      const bool from_b = nf0 >= kFromB;
+      const bool from_b = nf0 >= P.b_side_min;
       for (int64_t next = cb; next < ce; next += 32) {
         int32_t tag0 = 0;
         int len = 0, start = 0, tag1 = 0;
         {
           const int64_t ci = next + lane;
-          if (ci < ce) {
+          if (ci < ce && PGM_IDX_OK(ci, P.n_l3)) {
             const uint32_t e = P.l3[ci];
             const int32_t v2 = (int32_t)(e & kVidMask);
             const int a12 = (e & kA12) ? 1 : 0;
             const int t0 = (int)(ci - cb);
             const long long I_gt2 = ni - lower_bound_dev(I, ni, v2 + 1);  // |I & (v2, inf)|
             tag0 = v2;
-            if (t0 < nf0) {
+            if (t0 < nf0 && PGM_IDX_OK(a2_of(u0, j1, t0) - P.a_base, P.n_arc_slots)) {
               const int idx = j1 + 1 + t0;  // v2 = A[idx]
               const int64_t a2 = (int64_t)u0 + idx;
               const uint2 tr = P.tri[a2 - P.a_base];  // (|N(v2) & A|, |N(v2) & A & (v2, inf)|)
@@ -787,7 +798,7 @@ __global__ void __launch_bounds__(kML3Threads, 3) motif_l3_edge(MotifArgs P) {
           }
         }
         seen += (unsigned long long)len;
-        flat_scan<2>(P.col, len, start, tag0, tag1, Qe, Qs, lane, test, hit);
+        flat_scan<2>(P.col, P.narcs, len, start, tag0, tag1, Qe, Qs, lane, test, hit);
       }
       // fold the region moves into the pattern counters: for a12 = 0 the
       // regions (A only, B only, A&B, v2 only, A&v2, B&v2, all) are (3-star,
@@ -809,7 +820,7 @@ __global__ void __launch_bounds__(kML3Threads, 3) motif_l3_edge(MotifArgs P) {
 }
 
 // The common neighbours of v1 and v2 above v0 for the f2 = 0 children of
-// the level-2 edges (v0, v1) that have at least kFromB of them, found from
+// the level-2 edges (v0, v1) that have at least b_side_min of them, found from
 // B's side: every w in B = N(v1) & (v0, inf) is extended by N(w) above v1
 // (below w when w is in A), and each element v2 in A makes the pair (v2, w):
 // w in A & B above v2, or w in B \ A, for the child (v0, v1, v2) with a12 =
@@ -843,7 +854,7 @@ __global__ void __launch_bounds__(kML3Threads, 3) motif_l3_pairs(MotifArgs P) {
       const int32_t u0 = P.up[v0];
       const int s = P.rp[v0 + 1] - u0;
       const int nf0 = s - (int)(a - u0) - 1;
-      if (nf0 < kFromB) continue;  // motif_l3_edge scans these children itself
+      if (nf0 < P.b_side_min) continue;  // motif_l3_edge scans these children itself
       if (P.gid) {
         const int g = P.gid[v0];
         if (g != cur_g) {
@@ -905,11 +916,12 @@ __global__ void __launch_bounds__(kML3Threads, 3) motif_l3_pairs(MotifArgs P) {
           w_in_A = hArow ? row_bit(hArow, w) : member(A, s, -1, P, w);
           // N(w) above v1 starts after the reverse arc (w, v1) of arc (v1, w); below
           // w it ends at up[w], the first neighbour of w above w
-          start = P.rev[(int64_t)r0 + bstart + w0 + lane] + 1;
+          const int64_t ab = (int64_t)r0 + bstart + w0 + lane;  // arc (v1, w)
+          start = PGM_IDX_OK(ab, P.narcs) ? P.rev[ab] + 1 : 0;
           len = max((w_in_A ? P.up[w] : P.rp[w + 1]) - start, 0);
         }
         seen += (unsigned long long)len;
-        flat_scan<4>(P.col, len, start, w, w_in_A, Qe, Qs, lane, test, hit);
+        flat_scan<4>(P.col, P.narcs, len, start, w, w_in_A, Qe, Qs, lane, test, hit);
       }
       // region moves (see motif_l3_edge): y1 = A & B & v2, y2 = B & v2 (not A)
       c[0] += y1a;
@@ -967,6 +979,9 @@ struct MotifRun {
     P.hub_words = g.hub_words;
     P.rev = g.rev;
     P.tri = ws.tri.p;
+    P.carry = ctr() + kCarrySlot;
+    P.narcs = g.narcs;
+    P.n_arc_slots = g.h_rp[v_hi] - g.h_rp[v_lo];
     return P;
   }
 
@@ -1017,6 +1032,7 @@ struct MotifRun {
     P.hub_words = g.hub_words;
     const int threads = std::min(o.block_threads, kML3Threads);
     P.cap = std::min(cap, kML3Cap);
+    P.b_side_min = o.motif_b_side_min > 0 ? o.motif_b_side_min : 32;
     // (threads / 32) warps of at most 5.8 KB: four blocks fit an SM
     const size_t wsmem = (size_t)(threads / 32) * ml3_warp_ints(P.cap) * sizeof(int32_t);
     PGM_TRY(smem_attr((const void*)motif_l3_edge, (int)std::max<size_t>(wsmem, 200 * 1024)));
@@ -1044,6 +1060,7 @@ struct MotifRun {
     PGM_TRY(ws.big.reserve((size_t)g.n / 2 + 2));  // every vertex fits (as int32)
     PGM_TRY(ws.ctr.reserve(kNSlots));
     PGM_TRY_CUDA(cudaMemsetAsync(ctr(), 0, kNSlots * sizeof(unsigned long long), s));
+    if (!per_graph) PGM_TRY(seed_counts(ctr() + kAcc, k == 3 ? 2 : 6, s));
     return PGM_OK;
   }
 
@@ -1103,6 +1120,8 @@ struct MotifRun {
         W.off = ws.off[2].p;
         W.off_shift = base;
         W.l3 = reinterpret_cast<uint32_t*>(ws.vid[3].p);
+        W.n_l3 = Tp;
+        W.n_arc_slots = E;
         PGM_TRY(launch_l2<mWrite>(W, "extend_write"));
         PGM_TRY(launch_l3(W, pa, pb, (double)Tp));
       }
@@ -1160,8 +1179,12 @@ pgm_status count_motifs_on(Graph& g, Workspace& ws, cudaStream_t s, int k, int32
     set_error("count_motifs: internal hub-list overflow");
     return PGM_ENOMEM;
   }
+  if (h[kCarrySlot]) {
+    set_error("count_motifs: a count exceeds 2^64 - 1");
+    return PGM_EOVERFLOW;
+  }
   const int np = k == 3 ? 2 : 6;
-  for (int i = 0; i < np; i++) out[i] = h[kAcc + i];
+  for (int i = 0; i < np; i++) out[i] = h[kAcc + i] - (per_graph_dev ? 0ull : count_seed());
   pgm_profile& lp = last_profile();
   Profiler& prof = profiler();
   if (prof.on) {

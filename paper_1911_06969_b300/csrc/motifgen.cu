@@ -155,6 +155,7 @@ struct MgArgs {
   unsigned long long* per_graph;  // batches: 21 class counts per graph (hist mode)
   unsigned long long* queue;
   unsigned long long* stat;  // neighbour elements scanned
+  unsigned long long* carry; // wraps of the count accumulators (add_count)
 };
 
 // a[j] for a runtime j < N, without dynamic indexing (keeps `a` in registers)
@@ -302,7 +303,8 @@ __global__ void __launch_bounds__(256) mg_extend(MgArgs A) {
           const unsigned same = __match_any_sync(kFull, cls);
           if (cls >= 0 && lane == __ffs(same) - 1) {
             if (A.per_graph)
-              atomicAdd(A.per_graph + (int64_t)A.gid[v[0]] * kP5 + cls, (unsigned long long)__popc(same));
+              add_count(A.per_graph + (int64_t)A.gid[v[0]] * kP5 + cls, (unsigned long long)__popc(same), false,
+                        A.carry);
             else
               atomicAdd(&hist[cls], (unsigned long long)__popc(same));
           }
@@ -334,7 +336,7 @@ __global__ void __launch_bounds__(256) mg_extend(MgArgs A) {
   if (MODE == mgHist) {
     __syncthreads();
     for (int t = threadIdx.x; t < kP5; t += blockDim.x)
-      if (hist[t]) atomicAdd(A.hist + t, hist[t]);
+      if (hist[t]) add_count(A.hist + t, hist[t], false, A.carry);
   }
   seen = warp_sum(seen);
   if (lane == 0 && seen) atomicAdd(A.stat, seen);
@@ -367,6 +369,7 @@ struct MgRun {
     A.err = ws.ctr.p + kErrg;
     A.hist = ws.ctr.p + kHistg;
     A.stat = ws.ctr.p + kStatg + I;
+    A.carry = ws.ctr.p + kCarrySlot;
     PGM_TRY_CUDA(cudaMemsetAsync(A.queue, 0, sizeof(unsigned long long), s));
     const int64_t n = A.p_hi - A.p_lo;
     if (n <= 0) return PGM_OK;
@@ -492,6 +495,7 @@ struct MgRun {
     PGM_TRY(graph_prepare_motifs(g));
     PGM_TRY(ws.ctr.reserve(kSlotsg));
     PGM_TRY_CUDA(cudaMemsetAsync(ws.ctr.p, 0, kSlotsg * sizeof(unsigned long long), s));
+    if (!per_graph) PGM_TRY(seed_counts(ws.ctr.p + kHistg, kP5, s));
     const int64_t a_lo = g.h_rp[v_lo], a_hi = g.h_rp[v_hi];
     PGM_TRY(level(2, nullptr, a_hi - a_lo, a_lo));
     PGM_TRY(read_counters(ws.ctr.p, h, kSlotsg, s, deferred));
@@ -516,8 +520,12 @@ pgm_status count_motifs5(Graph& g, Workspace& ws, cudaStream_t s, int32_t v_lo, 
   bool deferred = false;
   PGM_TRY(run.run(v_lo, v_hi, h, &deferred));
   if (deferred) return PGM_OK;
+  if (h[kCarrySlot]) {
+    set_error("count_motifs: a count exceeds 2^64 - 1");
+    return PGM_EOVERFLOW;
+  }
   uint64_t t = 0;
-  for (int c = 0; c < kP5; c++) t += out[c] = h[kHistg + c];
+  for (int c = 0; c < kP5; c++) t += out[c] = h[kHistg + c] - (per_graph_dev ? 0ull : count_seed());
   last_profile().level_size[5] = t;
   return PGM_OK;
 }

@@ -102,6 +102,7 @@ extern "C" pgm_status pgm_count_triangles_noalloc(int32_t n, const int32_t* dag_
     A.stat = sc->ctr + kNaStat;
     A.queue = sc->ctr + kNaQueue;
     A.err = sc->ctr + kNaErr;
+    A.carry = sc->ctr + kCarrySlot;
     A.big = sc->big;
     A.big_cap = big_need;
     A.hub = hub;
@@ -126,12 +127,17 @@ extern "C" pgm_status pgm_count_triangles_noalloc(int32_t n, const int32_t* dag_
   }
   PGM_TRY_CUDA(cudaMemcpyAsync(count_dev, sc->ctr + kNaAcc, sizeof(unsigned long long),
                                cudaMemcpyDeviceToDevice, s));
-  unsigned long long err = 0;
+  unsigned long long err = 0, carry = 0;
   PGM_TRY_CUDA(cudaMemcpyAsync(&err, sc->ctr + kNaErr, sizeof(err), cudaMemcpyDeviceToHost, s));
+  PGM_TRY_CUDA(cudaMemcpyAsync(&carry, sc->ctr + kCarrySlot, sizeof(carry), cudaMemcpyDeviceToHost, s));
   PGM_TRY_CUDA(cudaStreamSynchronize(s));
   if (err) {
     set_error("pgm_count_triangles_noalloc: hub list overflow");
     return PGM_ENOMEM;
+  }
+  if (carry) {
+    set_error("pgm_count_triangles_noalloc: the count exceeds 2^64 - 1");
+    return PGM_EOVERFLOW;
   }
   return PGM_OK;
 }

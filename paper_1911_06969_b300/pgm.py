@@ -17,7 +17,8 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libpgm.so")
+# PGM_LIB=debug loads the bounds-checked build (libpgm_debug.so, see build.py)
+LIB_PATH = os.path.join(_HERE, "libpgm_debug.so" if os.environ.get("PGM_LIB") == "debug" else "libpgm.so")
 
 PGM_OK = 0
 PGM_EINVAL = -1
@@ -57,7 +58,7 @@ class pgm_options(C.Structure):
                 ("blocks_per_sm", C.c_int32), ("level_budget", C.c_int64), ("profile", C.c_int32),
                 ("reverse_ratio", C.c_int32), ("clique_engine", C.c_int32),
                 ("bitset_forward_ratio", C.c_int32), ("bitset_smem_degree", C.c_int32),
-                ("motif_order", C.c_int32), ("reserved", C.c_int32 * 2)]
+                ("motif_order", C.c_int32), ("count_headroom_log2", C.c_int32), ("motif_b_side_min", C.c_int32)]
 
 
 class pgm_phase(C.Structure):
@@ -72,10 +73,15 @@ class pgm_profile(C.Structure):
 
 class pgm_tune(C.Structure):
     _fields_ = [("block_threads", C.c_int32), ("warp_stage_cap", C.c_int32), ("hub_threshold", C.c_int32),
-                ("blocks_per_sm", C.c_int32), ("use_graph", C.c_int32), ("reserved", C.c_int32 * 3)]
+                ("blocks_per_sm", C.c_int32), ("use_graph", C.c_int32), ("motif_b_side_min", C.c_int32),
+                ("reverse_ratio", C.c_int32), ("bitset_forward_ratio", C.c_int32)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+
+
+class pgm_tune_trial(C.Structure):
+    _fields_ = [("tune", pgm_tune), ("ms", C.c_double)]
 
 
 class pgm_query(C.Structure):
@@ -107,6 +113,9 @@ _SIGS = {
     "pgm_batch_count_kcliques": (C.c_int, [P, C.c_int32, P, C.POINTER(pgm_tune)]),
     "pgm_batch_count_motifs_loop": (C.c_int, [P, C.c_int32, P]),
     "pgm_batch_autotune": (C.c_int, [P, C.c_int32, C.POINTER(pgm_tune), C.POINTER(C.c_double)]),
+    "pgm_batch_autotune_ex": (C.c_int, [P, C.c_int32, C.c_char_p, C.POINTER(pgm_tune), C.POINTER(C.c_double),
+                                        C.POINTER(pgm_tune_trial), C.c_int32, C.POINTER(C.c_int32),
+                                        C.POINTER(C.c_int32)]),
     "pgm_batch_size": (C.c_int32, [P]),
     "pgm_batch_destroy": (None, [P]),
     "pgm_server_create": (C.c_int, [C.c_int64, C.c_int32, C.POINTER(P)]),
@@ -122,6 +131,7 @@ _SIGS = {
     "pgm_last_error": (C.c_char_p, []),
     "pgm_version": (C.c_char_p, []),
     "pgm_kernel_launches": (C.c_uint64, []),
+    "pgm_debug_errors": (C.c_uint64, [C.c_int32]),
     "pgm_count_triangles_noalloc": (C.c_int, [C.c_int32, P, P, C.c_int64, P, P]),
 }
 
@@ -316,6 +326,19 @@ def pgm_batch_autotune(b: int, k: int):
     return t, float(ms.value)
 
 
+def pgm_batch_autotune_ex(b: int, k: int, cache_path: str | None = None, cap: int = 64):
+    """(best tune, best ms, [(tune dict, ms) per timed trial], came from the cache)."""
+    t = pgm_tune()
+    ms = C.c_double()
+    tr = (pgm_tune_trial * max(cap, 1))()
+    n = C.c_int32()
+    hit = C.c_int32()
+    path = cache_path.encode() if cache_path else None
+    _ok(load().pgm_batch_autotune_ex(b, k, path, C.byref(t), C.byref(ms), tr, cap, C.byref(n), C.byref(hit)),
+        "pgm_batch_autotune_ex")
+    return t, float(ms.value), [(tr[i].tune.as_dict(), float(tr[i].ms)) for i in range(n.value)], bool(hit.value)
+
+
 def pgm_batch_size(b: int) -> int:
     return int(load().pgm_batch_size(b))
 
@@ -382,6 +405,11 @@ def pgm_get_options() -> dict:
     o = pgm_options()
     _ok(load().pgm_get_options(C.byref(o)), "pgm_get_options")
     return {f: getattr(o, f) for f, _ in pgm_options._fields_ if f != "reserved"}
+
+
+def pgm_debug_errors(reset: bool = False) -> int:
+    """Out-of-range indices met by the bounds-checked build (always 0 otherwise)."""
+    return int(load().pgm_debug_errors(1 if reset else 0))
 
 
 def pgm_last_profile() -> dict:

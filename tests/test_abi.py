@@ -41,3 +41,15 @@ def test_host_only_calls():
         pgm.pgm_set_options(level_budget=5)
     assert lib.pgm_batch_size(None) == 0
     assert pgm.pgm_get_options()["block_threads"] == 256
+
+
+def test_debug_library_exports_header():
+    """The bounds-checked variant (PGM_DEBUG) exports the same ABI; without a
+    device its error query reads no word and reports 0."""
+    path = build.build(debug=True)
+    lib = ctypes.CDLL(path)
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+    lib.pgm_debug_errors.restype = ctypes.c_uint64
+    lib.pgm_debug_errors.argtypes = [ctypes.c_int32]
+    assert lib.pgm_debug_errors(0) == 0

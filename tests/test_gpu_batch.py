@@ -65,6 +65,34 @@ def test_graph_replay_and_autotune():
         pgm.pgm_batch_destroy(h)
 
 
+def test_autotune_trials_and_cache(tmp_path):
+    """pgm_batch_autotune_ex: the first call times candidates (every trial
+    listed, the winner the fastest of them, counts exact under it) and
+    writes the winner to a JSON cache keyed by the batch's features; the
+    second call returns the same setting from the cache without timing."""
+    import json
+
+    b = gg.batch_small(200, nmin=16, nmax=400, seed=6)
+    h = make_batch(b)
+    cache = str(tmp_path / "tune.json")
+    try:
+        want = oracle.formula_motifs_batch(b, 4)
+        t1, ms1, trials, hit1 = pgm.pgm_batch_autotune_ex(h, 4, cache)
+        assert not hit1 and len(trials) >= 8
+        assert ms1 == min(ms for _, ms in trials)
+        assert t1.use_graph == 1
+        assert np.array_equal(pgm.pgm_batch_count_motifs(h, 4, t1), want)
+        for tt, _ in trials:  # every knob combination tried gives the same counts
+            t = pgm.pgm_tune(**{k: v for k, v in tt.items() if k != "use_graph"})
+            assert np.array_equal(pgm.pgm_batch_count_motifs(h, 4, t), want), tt
+        t2, ms2, trials2, hit2 = pgm.pgm_batch_autotune_ex(h, 4, cache)
+        assert hit2 and trials2 == [] and t2.as_dict() == t1.as_dict() and abs(ms2 - ms1) < 1e-2
+        entries = json.load(open(cache))
+        assert len(entries) == 1 and list(entries)[0].startswith("motif4_G2^7_")
+    finally:
+        pgm.pgm_batch_destroy(h)
+
+
 def test_batch_rejects_crossing_arcs():
     g = gg.path(6)  # vertices 0..5; split as two graphs of 3 -> arc 2-3 crosses
     with pytest.raises(pgm.PgmError) as e:

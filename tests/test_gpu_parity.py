@@ -377,6 +377,7 @@ def test_bitset_deep(smem_degree):
     import itertools
     import math
 
+    saved = pgm.pgm_get_options()
     pgm.pgm_set_options(clique_engine=2, bitset_smem_degree=smem_degree)
     try:
         for g, ks in [(gg.rmat(1 << 12, 40000, seed=42), (6, 7, 8, 9)),
@@ -399,10 +400,43 @@ def test_bitset_deep(smem_degree):
             sizes = pgm.pgm_last_profile()["level_size"]
         assert sizes[1:9] == oracle.clique_levels(g, 8, "degree", threads=8)[1:9]
     finally:
-        pgm.pgm_set_options(clique_engine=0, bitset_smem_degree=1024, profile=0)
+        pgm.pgm_set_options(**saved)
     pgm.pgm_set_options(clique_engine=1)
     try:
         g = gg.rmat(1 << 12, 40000, seed=42)
         assert gpu_cliques(g, [6, 7]) == [oracle.clique_count(g, k, "degree", threads=8) for k in (6, 7)]
     finally:
-        pgm.pgm_set_options(clique_engine=0)
+        pgm.pgm_set_options(**saved)
+
+
+@pytest.mark.parametrize("engine", [1, 2])
+def test_count_overflow_status(engine):
+    """PGM_EOVERFLOW: with the accumulators started 2^x below 2^64
+    (options.count_headroom_log2 = x), a count below 2^x comes back exact
+    and a count of 2^x or more fails with PGM_EOVERFLOW -- for clique counts
+    on both engines and for motif counts (k = 3, 4, 5), whose per-warp
+    partials are signed (region corrections).  No fault is involved: the
+    start value is an ordinary host write."""
+    saved = pgm.pgm_get_options()
+    d = json.load(open(os.path.join(GOLD, "triangle_er.json")))
+    gc = gg.barabasi_albert(2000, 8, seed=17)
+    g5 = gg.erdos_renyi(200, 0.05, seed=9)
+    cases = [(gc, "kcliques", k, [oracle.clique_count(gc, k, "degree", threads=8)]) for k in (3, 4, 5)]
+    cases += [(gg.triangle_er(), "motifs", k, d[f"motif{k}"]) for k in (3, 4)]
+    cases += [(g5, "motifs", 5, oracle.esu_motifs(g5, 5))]
+    try:
+        for g, fn, k, want in cases:
+            x = max(want).bit_length()  # the largest count is in [2^(x-1), 2^x)
+            assert x >= 2, (g.name, k)
+            with pgm.Graph(g) as G:
+                call = (lambda: [G.kcliques(k)]) if fn == "kcliques" else (lambda: G.motifs(k))
+                pgm.pgm_set_options(clique_engine=engine, count_headroom_log2=x)
+                assert call() == want, (g.name, fn, k)
+                pgm.pgm_set_options(clique_engine=engine, count_headroom_log2=x - 1)
+                with pytest.raises(pgm.PgmError) as e:
+                    call()
+                assert e.value.status == pgm.PGM_EOVERFLOW, (g.name, fn, k)
+                pgm.pgm_set_options(clique_engine=engine, count_headroom_log2=0)
+                assert call() == want, (g.name, fn, k)
+    finally:
+        pgm.pgm_set_options(**saved)
