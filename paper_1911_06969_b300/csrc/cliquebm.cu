@@ -414,15 +414,17 @@ constexpr int kBmGlobalFW = 8192;
 // Set bits of a row, 32 at a time: appends the set bits of the 32 words
 // held one per lane (`mine`, words w0 .. w0 + 31) to the warp's buffer
 // (64 entries) and calls f(j, true) on every lane for each full group of
-// 32 positions j.  bm_bits_tail() hands over the last partial group.
+// 32 positions j.  bm_bits_tail() hands over the last partial group.  A
+// non-zero `tag` (< 2^15, rows of fewer than 2^16 positions) is stored in
+// bits 16.. of each entry.
 template <class F>
-__device__ __forceinline__ void bm_bits(uint32_t mine, int w0, int* buf, int& cnt, int lane, F& f) {
+__device__ __forceinline__ void bm_bits(uint32_t mine, int w0, int* buf, int& cnt, int lane, F& f, int tag = 0) {
   uint32_t nz = __ballot_sync(kFull, mine != 0u);
   while (nz) {
     const int q = __ffs(nz) - 1;
     nz &= nz - 1;
     const uint32_t word = __shfl_sync(kFull, mine, q);
-    if ((word >> lane) & 1u) buf[cnt + __popc(word & ((1u << lane) - 1u))] = ((w0 + q) << 5) + lane;
+    if ((word >> lane) & 1u) buf[cnt + __popc(word & ((1u << lane) - 1u))] = (tag << 16) + ((w0 + q) << 5) + lane;
     cnt += __popc(word);
     if (cnt >= 32) {
       __syncwarp();
@@ -476,10 +478,18 @@ __host__ __device__ constexpr size_t bm_block_smem(int dmax, int threads, int cl
                   : (size_t)4 * (threads / 32) * 128 + (size_t)4 * kBmGlobalFW;
 }
 
+// C buffers per warp of the 5-clique count: one per j of a group of j's
+// processed together (8 for out-degrees up to 256, 2 up to 512, else 1).
+__host__ __device__ constexpr int bm_c5(int dmax) { return dmax == 256 ? 8 : (dmax == 512 ? 2 : 1); }
+
+// The largest block layout, k = 10 (kDeepMax C buffers) in the 1024 bucket,
+// is 220,160 B: within the 227 KB a block may opt into on sm_103a.
+static_assert(bm_block_smem(1024, 1024, kDeepMax) <= 227 * 1024, "bitset bucket exceeds 227 KB");
+
 // resident blocks per SM that the register budget is sized for (the walk
 // of k >= 6 keeps its level counters in registers: fewer, larger threads)
 __host__ __device__ constexpr int bm_min_blocks(int dmax, int threads, int kv) {
-  return kv == 6 ? (threads <= 256 ? 4 : (threads <= 512 ? 2 : 1))
+  return kv >= 5 ? (threads <= 256 ? 4 : (threads <= 512 ? 2 : 1))
                  : (dmax == 0 ? 2 : (threads <= 256 ? 8 : (threads <= 512 ? 3 : 1)));
 }
 
@@ -488,10 +498,16 @@ __host__ __device__ constexpr int bm_min_blocks(int dmax, int threads, int kv) {
 // to buffer T of the warp (cstride words apart); at depth D the leaf adds
 // |C_D & R_l| for every l in C_D, one l per lane.  lvl[t] counts the
 // entries of level t + 3.
+//
+// At depth D - 1 (children are leaves) with G > 1 the j's go in groups of G,
+// one group of 4 n4 lanes per j: C_D = C_T & R_j for the whole group into
+// buffers T .. T + G - 1, then the pairs (C_D, l) of the group 32 at a time
+// (buf2), so that the leaves of sibling chains share full warps.
 template <int T, class RowFn>
 __device__ __forceinline__ void bm_deep_walk(const uint32_t* Ct, int D, int W, int n4, uint32_t* Cbuf,
-                                             int64_t cstride, const RowFn& row4, int* buf, int lane,
-                                             unsigned long long& leaf, unsigned long long (&lvl)[kDeepMax + 1]) {
+                                             int64_t cstride, const RowFn& row4, int* buf, int* buf2, int G,
+                                             int lane, unsigned long long& leaf,
+                                             unsigned long long (&lvl)[kDeepMax + 1]) {
   if (T == D) {
     int cnt = 0;
     auto fl = [&](int l, bool valid) {
@@ -505,6 +521,43 @@ __device__ __forceinline__ void bm_deep_walk(const uint32_t* Ct, int D, int W, i
     return;
   }
   if constexpr (T < kDeepMax) {
+    if (T + 1 == D && G > 1) {
+      const int L = 4 * n4;
+      uint32_t* Cg0 = Cbuf + (int64_t)T * cstride;  // buffers T .. T + G - 1
+      auto fl = [&](int e, bool v) {
+        if (v) leaf += bm_and_popc4(reinterpret_cast<const uint4*>(Cg0 + (int64_t)(e >> 16) * cstride), row4(e & 0xffff), n4);
+      };
+      auto fj = [&](int j, bool valid) {
+        const int nvj = __popc(__ballot_sync(kFull, valid));  // valid lanes are a prefix
+        for (int g0 = 0; g0 < nvj; g0 += G) {
+          const int ng = min(G, nvj - g0);
+          const int gi = lane / L, w = lane - gi * L;
+          const int jq = __shfl_sync(kFull, j, min(g0 + gi, 31));
+          unsigned cn = 0;
+          if (gi < ng) {
+            const uint32_t x = Ct[w] & reinterpret_cast<const uint32_t*>(row4(jq))[w];  // padding words are zero
+            Cg0[gi * cstride + w] = x;
+            cn = __popc(x);
+          }
+          lvl[T + 1] += cn;
+          __syncwarp();
+          int cnt2 = 0;
+          for (int g = 0; g < ng; g++)
+            for (int w0 = 0; w0 < W; w0 += 32) {
+              const uint32_t mine = w0 + lane < W ? Cg0[g * cstride + w0 + lane] : 0u;
+              bm_bits(mine, w0, buf2, cnt2, lane, fl, g);
+            }
+          bm_bits_tail(buf2, cnt2, lane, fl);  // ends with __syncwarp: the group's buffers are free
+        }
+      };
+      int cnt = 0;
+      for (int w0 = 0; w0 < W; w0 += 32) {
+        const uint32_t mine = w0 + lane < W ? Ct[w0 + lane] : 0u;
+        bm_bits(mine, w0, buf, cnt, lane, fj);
+      }
+      bm_bits_tail(buf, cnt, lane, fj);
+      return;
+    }
     uint32_t* Cn = Cbuf + (int64_t)T * cstride;  // C_{T+1}
     for (int w0 = 0; w0 < W; w0 += 32) {
       const uint32_t mine = w0 + lane < W ? Ct[w0 + lane] : 0u;
@@ -527,7 +580,7 @@ __device__ __forceinline__ void bm_deep_walk(const uint32_t* Ct, int D, int W, i
           lvl[T + 1] += cn;
           __syncwarp();
           if (__any_sync(kFull, cn != 0u))
-            bm_deep_walk<T + 1>(Cn, D, W, n4, Cbuf, cstride, row4, buf, lane, leaf, lvl);
+            bm_deep_walk<T + 1>(Cn, D, W, n4, Cbuf, cstride, row4, buf, buf2, G, lane, leaf, lvl);
         }
       }
     }
@@ -553,7 +606,9 @@ __global__ void __launch_bounds__(THREADS, bm_min_blocks(DMAX, THREADS, KV)) bm_
   uint16_t* sPos = reinterpret_cast<uint16_t*>(smem_u + 6 * DMAX);
   int* buf = reinterpret_cast<int*>(smem_u) + kHead + wid * 128;
   int* buf2 = buf + 64;
-  const int CL = KV == 6 ? B.clevels : 1;  // C buffers per warp
+  // C buffers per warp: 5-cliques, one per j of a group; the walk, one per
+  // depth plus the extra buffers of the grouped last level
+  const int CL = KV == 6 ? B.clevels - 1 + bm_c5(DMAX) : (KV == 5 ? bm_c5(DMAX) : 1);
   uint32_t* sC = smem_u + kHead + NW * 128 + wid * 4 * S4MAX * CL;
   uint32_t* sRows = smem_u + kHead + NW * 128 + NW * 4 * S4MAX * CL;
   uint32_t* gRows = B.scratch ? B.scratch + (int64_t)blockIdx.x * B.scratch_words : nullptr;
@@ -671,7 +726,9 @@ __global__ void __launch_bounds__(THREADS, bm_min_blocks(DMAX, THREADS, KV)) bm_
       c[1] += tri;
       int cnt = 0;
       if constexpr (KV == 6) {
-        bm_deep_walk<0>(Ri, B.k - 4, W, n4, C, cstride, row4, buf, lane, c[0], lvl);
+        const int L = 4 * n4;
+        bm_deep_walk<0>(Ri, B.k - 4, W, n4, C, cstride, row4, buf, buf2, L <= 32 ? min(32 / L, bm_c5(DMAX)) : 1,
+                        lane, c[0], lvl);
       } else if constexpr (KV == 4) {
         // 4-cliques: |R_i & R_j| for every j in R_i, one j per lane
         auto f4 = [&](int j, bool valid) {
@@ -685,27 +742,51 @@ __global__ void __launch_bounds__(THREADS, bm_min_blocks(DMAX, THREADS, KV)) bm_
       } else {
         // 5-cliques: for each j in R_i (one at a time), C = R_i & R_j; then
         // |C & R_l| for every l in C, one l per lane
+        // 5-cliques: the j's of R_i in groups of G, one group of L = 4 n4 lanes
+        // per j (G = 32 / L, at most the warp's C buffers): C_j = R_i & R_j for
+        // the whole group in one pass, then the pairs (C_j, l), l in C_j, of the
+        // group 32 at a time, |C_j & R_l| one pair per lane
+        const int L = 4 * n4;
+        const int G = L <= 32 ? min(32 / L, CL) : 1;
+        auto f5l = [&](int e, bool v2) {
+          if (v2) {
+            const uint32_t* Cg = C + (int64_t)(G > 1 ? (e >> 16) : 0) * cstride;
+            c[0] += bm_and_popc4(reinterpret_cast<const uint4*>(Cg), row4(G > 1 ? (e & 0xffff) : e), n4);
+          }
+        };
         auto f5 = [&](int j, bool valid) {
-          for (unsigned mq = __ballot_sync(kFull, valid); mq; mq &= mq - 1) {
-            const int q = __ffs(mq) - 1;
-            const int jq = __shfl_sync(kFull, j, q);
-            const uint32_t* Rj = reinterpret_cast<const uint32_t*>(row4(jq));
-            unsigned cnt4 = 0;
-            for (int w = lane; w < 4 * n4; w += 32) {
-              const uint32_t x = Ri[w] & Rj[w];  // padding words are zero
-              C[w] = x;
-              cnt4 += __popc(x);
+          const int nvj = __popc(__ballot_sync(kFull, valid));  // valid lanes are a prefix
+          for (int g0 = 0; g0 < nvj; g0 += G) {
+            const int ng = min(G, nvj - g0);
+            if (G > 1) {
+              const int gi = lane / L, w = lane - gi * L;
+              const int jq = __shfl_sync(kFull, j, min(g0 + gi, 31));
+              unsigned cnt4 = 0;
+              if (gi < ng) {
+                const uint32_t x = Ri[w] & reinterpret_cast<const uint32_t*>(row4(jq))[w];  // padding words are zero
+                C[gi * cstride + w] = x;
+                cnt4 = __popc(x);
+              }
+              c[2] += cnt4;
+            } else {
+              const int jq = __shfl_sync(kFull, j, g0);
+              const uint32_t* Rj = reinterpret_cast<const uint32_t*>(row4(jq));
+              unsigned cnt4 = 0;
+              for (int w = lane; w < L; w += 32) {
+                const uint32_t x = Ri[w] & Rj[w];
+                C[w] = x;
+                cnt4 += __popc(x);
+              }
+              c[2] += cnt4;
             }
-            c[2] += cnt4;
             __syncwarp();
             int cnt2 = 0;
-            auto f5l = [&](int l, bool v2) {
-              if (v2)
-                c[0] += bm_and_popc4(reinterpret_cast<const uint4*>(C), row4(l), n4);
-            };
-            for (int w0 = 0; w0 < W; w0 += 32) {
-              const uint32_t mine = w0 + lane < W ? C[w0 + lane] : 0u;
-              bm_bits(mine, w0, buf2, cnt2, lane, f5l);
+            for (int gi = 0; gi < ng; gi++) {
+              const uint32_t* Cg = C + (int64_t)gi * cstride;
+              for (int w0 = 0; w0 < W; w0 += 32) {
+                const uint32_t mine = w0 + lane < W ? Cg[w0 + lane] : 0u;
+                bm_bits(mine, w0, buf2, cnt2, lane, f5l, gi);
+              }
             }
             bm_bits_tail(buf2, cnt2, lane, f5l);
           }
@@ -731,6 +812,28 @@ __global__ void __launch_bounds__(THREADS, bm_min_blocks(DMAX, THREADS, KV)) bm_
 
 }  // namespace
 
+// Words of row scratch per block of the global-row bucket: d rows plus 16
+// warps' C buffers (1, or k - 4 for the walk of k >= 6), 4 * S4 words each.
+int64_t bitset_row_words(int64_t dmax, int k) {
+  const int clevels = k >= 6 ? k - 4 : 1;
+  return (dmax + 16 * (int64_t)clevels) * 4 * (int64_t)bm_s4((int)((dmax + 31) / 32));
+}
+
+// Device bytes of that scratch for a count on g (0 when every out-list fits
+// the shared-memory rows): the bucket kernel's persistent grid x the words
+// per block, as count_kcliques_bitset reserves them.
+int64_t bitset_scratch_bytes(const Graph& g, int k) {
+  const int smem_d = options().bitset_smem_degree;
+  if (k < 3 || g.dag_dmax <= smem_d) return 0;
+  const int kv = k <= 4 ? 4 : (k == 5 ? 5 : 6);
+  const int clevels = kv == 6 ? k - 4 : 1;
+  const void* fn = kv == 4 ? (const void*)bm_block_kernel<0, 512, 4>
+                           : (kv == 5 ? (const void*)bm_block_kernel<0, 512, 5> : (const void*)bm_block_kernel<0, 512, 6>);
+  const size_t smem = bm_block_smem(0, 512, clevels);
+  if (smem_attr(fn, (int)smem) != PGM_OK) return 0;
+  return (int64_t)grid_for(fn, 512, smem) * bitset_row_words(g.dag_dmax, k) * 4;
+}
+
 // Bitset engine entry: counts k-cliques (k in 3..10) rooted in [v_lo, v_hi).
 // Returns PGM_EUNSUPPORTED when the DAG's largest out-degree would need more
 // than `max_scratch` bytes of row scratch (the caller then uses the
@@ -742,7 +845,6 @@ pgm_status count_kcliques_bitset(Graph& g, Workspace& ws, cudaStream_t s, int k,
   const pgm_options o = options();
   const int smem_d = o.bitset_smem_degree;
   const int64_t dmax = g.dag_dmax;
-  const int64_t Wmax = (dmax + 31) / 32;
   // bucket kernels: (64, 256], (256, 512], (512, 1024] with rows in shared
   // memory (each only up to smem_d), and the rest with rows in global memory
   struct Kern {
@@ -753,29 +855,44 @@ pgm_status count_kcliques_bitset(Graph& g, Workspace& ws, cudaStream_t s, int k,
   };
   const int kv = k <= 4 ? 4 : (k == 5 ? 5 : 6);
   const int clevels = kv == 6 ? k - 4 : 1;
+  // C buffers per warp of each bucket (5-cliques: a group of j's at once)
+  auto cl = [&](int dm) { return kv == 5 ? bm_c5(dm) : (kv == 6 ? clevels - 1 + bm_c5(dm) : clevels); };
   auto pick = [kv](const void* f4, const void* f5, const void* f6) { return kv == 4 ? f4 : (kv == 5 ? f5 : f6); };
   Kern kern[kBmBuckets] = {
       {pick((const void*)bm_block_kernel<256, 256, 4>, (const void*)bm_block_kernel<256, 256, 5>,
             (const void*)bm_block_kernel<256, 256, 6>),
-       256, bm_block_smem(256, 256, clevels), 0},
+       256, bm_block_smem(256, 256, cl(256)), 0},
       {pick((const void*)bm_block_kernel<512, 512, 4>, (const void*)bm_block_kernel<512, 512, 5>,
             (const void*)bm_block_kernel<512, 512, 6>),
-       512, bm_block_smem(512, 512, clevels), 0},
+       512, bm_block_smem(512, 512, cl(512)), 0},
       {pick((const void*)bm_block_kernel<1024, 1024, 4>, (const void*)bm_block_kernel<1024, 1024, 5>,
             (const void*)bm_block_kernel<1024, 1024, 6>),
-       1024, bm_block_smem(1024, 1024, clevels), 0},
+       1024, bm_block_smem(1024, 1024, cl(1024)), 0},
       {pick((const void*)bm_block_kernel<0, 512, 4>, (const void*)bm_block_kernel<0, 512, 5>,
             (const void*)bm_block_kernel<0, 512, 6>),
        512, bm_block_smem(0, 512, clevels), 0},
   };
   const void* warp_fn = kv == 6 ? (const void*)bm_warp_kernel<true> : (const void*)bm_warp_kernel<false>;
 
+  // buckets this count launches (largest out-degree first, see below); a
+  // bucket whose shared memory exceeds the device's per-block opt-in limit
+  // makes the engine decline (the caller falls back to the level lists)
+  bool used[kBmBuckets];
+  for (int b = 0; b < kBmBuckets; b++) used[b] = b < 3 ? (b == 0 ? 64 : (b == 1 ? 256 : 512)) < smem_d : dmax > smem_d;
+  int optin = 0;
+  PGM_TRY_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device_id()));
   for (int b = 0; b < kBmBuckets; b++) {
+    if (!used[b]) continue;
+    if (kern[b].smem > (size_t)optin) {
+      set_error("bitset engine: bucket %d needs %zu B of shared memory per block (device limit %d)", b,
+                kern[b].smem, optin);
+      return PGM_EUNSUPPORTED;
+    }
     PGM_TRY(smem_attr(kern[b].fn, (int)kern[b].smem));
     kern[b].grid = grid_for(kern[b].fn, kern[b].threads, kern[b].smem);
   }
   // global-row bucket: d rows plus 16 warps' C buffers per block, 4 * S4 words each
-  const int64_t words = dmax > smem_d ? (dmax + 16 * (int64_t)clevels) * 4 * (int64_t)bm_s4((int)Wmax) : 0;
+  const int64_t words = dmax > smem_d ? bitset_row_words(dmax, k) : 0;
   if (words > 0 && (double)kern[3].grid * (double)words * 4.0 > 8.0 * (double)(1ull << 30)) {
     set_error("bitset engine: out-degree %lld needs too much row scratch", (long long)dmax);
     return PGM_EUNSUPPORTED;
@@ -827,8 +944,7 @@ pgm_status count_kcliques_bitset(Graph& g, Workspace& ws, cudaStream_t s, int k,
     PGM_CHECK_LAUNCH();
     // largest rows first, so that the short tail of each launch is cheap
     for (int b = kBmBuckets - 1; b >= 0; b--) {
-      if (b < 3 && lo[b] >= smem_d) continue;  // bucket unused at this shared-memory limit
-      if (b == 3 && dmax <= smem_d) continue;
+      if (!used[b]) continue;  // bucket unused at this shared-memory limit
       const Kern& K = kern[b];
       void* argv[] = {&B, &b};
       PGM_TRY_CUDA(cudaLaunchKernel(K.fn, dim3(K.grid), dim3(K.threads), argv, K.smem, s));

@@ -308,6 +308,11 @@ pgm_status count_kcliques_bitset(Graph& g, Workspace& ws, cudaStream_t s, int k,
                                  uint64_t* level_sizes);
 pgm_status count_motifs(Graph& g, Workspace& ws, cudaStream_t s, int k, int32_t v_lo,
                         int32_t v_hi, uint64_t* out, unsigned long long* per_graph_dev);
+// device bytes of the bitset engine's global row scratch for a k-clique
+// count on g, as count_kcliques_bitset reserves it (0 if all rows fit in
+// shared memory); used by the server's memory prediction
+int64_t bitset_scratch_bytes(const Graph& g, int k);
+int64_t bitset_row_words(int64_t dmax, int k);
 
 // persistent-grid size for a kernel
 int grid_for(const void* fn, int threads, size_t smem);

@@ -81,10 +81,7 @@ int64_t predict_bytes(const pgm_server* s, const SGraph& sg, const pgm_query& q)
   if (clique && engine != 1) {
     // bitset levels: bucket lists, plus row scratch (rows and the warps' C
     // buffers, k - 4 of them for k >= 6) when out-lists exceed the shared-memory rows
-    const double dm = (double)g.dag_dmax, cl = k >= 6 ? (double)(k - 4) : 1.0;
-    b += 4.0 * n;
-    if (g.dag_dmax > pgm::options().bitset_smem_degree)
-      b += 2.0 * pgm::num_sms() * (dm + 16.0 * cl) * (std::ceil(dm / 128.0) + 1.0) * 16.0;
+    b += 4.0 * n + (double)pgm::bitset_scratch_bytes(g, k);
   } else if (clique && k >= 4) {
     b += 12.0 * (arcs / 2) + 16.0 * std::min(sg.c2_dag, budget_entries);
     if (k >= 5) b += 16.0 * budget_entries;  // deeper levels: at most one budget chunk each
