@@ -16,6 +16,11 @@ Functions and the passages they follow:
 * ``esu_motifs`` -- ESU enumeration (Wernicke 2006) of connected k-sets.
 * ``formula_motifs`` -- special-pattern counts plus pattern relationships
   (the "eliding isomorphism test" idea of Sec. 2.2).
+* ``fsm`` -- frequent subgraph mining (Sec. 2.1 FSM, Sec. 3.3 Listing 5):
+  connected edge sets of 1..3 edges enumerated once by shape, canonical
+  labelled patterns by brute force over vertex orders, MNI support from the
+  (pattern, automorphism orbit, vertex) triples; ``fsm_bf_support`` -- MNI
+  by brute-force subgraph matching (its textbook definition).
 * ``exclusive_scan`` -- the prefix-sum step of inspection-execution
   (Sec. 5.3); ``connectivity_mask`` -- the binary-search connectivity check
   (Sec. 5.4).
@@ -84,6 +89,10 @@ def _declare(lib):
     lib.orc_connectivity_mask.restype = ctypes.c_uint32
     lib.orc_connectivity_mask.argtypes = [P, P, I32, P, I32]
     lib.orc_degree_sums.argtypes = [I32, P, P, P, P]
+    lib.orc_fsm.restype = I32
+    lib.orc_fsm.argtypes = [I32, P, P, P, I32, I64, P, P, I32, P]
+    lib.orc_fsm_bf_support.restype = I32
+    lib.orc_fsm_bf_support.argtypes = [I32, P, P, P, I32, P, I32, P, P]
     return lib
 
 
@@ -202,6 +211,44 @@ def formula_motifs_batch(batch, k: int) -> np.ndarray:
                                        vo.ctypes.data, k, out.ctypes.data)
     _check(rc, "formula_motifs_batch")
     return out
+
+
+def fsm(g, labels, max_edges: int, min_support: int = 0) -> list:
+    """Frequent edge-induced labelled patterns of 1..max_edges (<= 3) edges
+    with MNI support >= min_support (Sec. 2.1, Sec. 3.3 Listing 5), ordered
+    by (edges, vertices, labels, adjacency); each a dict with the canonical
+    pattern (vertex labels and adjacency bits over the pairs (0,1), (0,2),
+    (0,3), (1,2), (1,3), (2,3) in the order that makes (labels, bits)
+    smallest), its support and its number of embeddings."""
+    rp, col = _arrs(g)
+    lab = np.ascontiguousarray(labels, np.int32)
+    assert lab.shape[0] == g.n
+    n = ctypes.c_int32()
+    _check(_L().orc_fsm(g.n, rp.ctypes.data, col.ctypes.data, lab.ctypes.data, max_edges, min_support,
+                        None, None, 0, ctypes.byref(n)), "fsm")
+    cap = max(n.value, 1)
+    meta = np.zeros((cap, 7), np.int32)
+    val = np.zeros((cap, 2), np.uint64)
+    _check(_L().orc_fsm(g.n, rp.ctypes.data, col.ctypes.data, lab.ctypes.data, max_edges, min_support,
+                        meta.ctypes.data, val.ctypes.data, cap, ctypes.byref(n)), "fsm")
+    out = []
+    for r in range(n.value):
+        nv = int(meta[r, 1])
+        out.append({"edges": int(meta[r, 0]), "labels": tuple(int(x) for x in meta[r, 2:2 + nv]),
+                    "adj": int(meta[r, 6]), "support": int(val[r, 0]), "embeddings": int(val[r, 1])})
+    return out
+
+
+def fsm_bf_support(g, labels, plabels, padj: int):
+    """(MNI support, matchings) of one pattern by brute-force subgraph
+    matching, the textbook definition (n <= 64)."""
+    rp, col = _arrs(g)
+    lab = np.ascontiguousarray(labels, np.int32)
+    pl = np.ascontiguousarray(plabels, np.int32)
+    s, m = ctypes.c_uint64(), ctypes.c_uint64()
+    _check(_L().orc_fsm_bf_support(g.n, rp.ctypes.data, col.ctypes.data, lab.ctypes.data, len(pl), pl.ctypes.data,
+                                   padj, ctypes.byref(s), ctypes.byref(m)), "fsm_bf_support")
+    return int(s.value), int(m.value)
 
 
 def exclusive_scan(counts) -> np.ndarray:

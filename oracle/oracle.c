@@ -35,6 +35,10 @@
  *   orc_esu_motifs  ESU enumeration (Wernicke, "Efficient detection of
  *                   network motifs", 2006): every connected k-set is
  *                   generated exactly once from its minimum vertex.
+ *   orc_fsm         frequent subgraph mining (edge-induced, vertex labels,
+ *                   MNI support, 1..3 edges): every connected edge set
+ *                   enumerated once by its shape; orc_fsm_bf_support is the
+ *                   matching-based MNI definition for tiny graphs.
  *   orc_formula_motifs  count special patterns directly, derive the rest
  *                   from the relationships among patterns (the "eliding
  *                   isomorphism test" idea of Sec. 2.2, PGD-style):
@@ -682,4 +686,377 @@ void orc_degree_sums(int32_t n, const int64_t *rp, uint64_t *c2_lo_hi, uint64_t 
   c3_lo_hi[0] = (uint64_t)s3;
   c3_lo_hi[1] = (uint64_t)(s3 >> 64);
   *dmax = m;
+}
+
+/* ------------------------------------------------ frequent subgraph mining
+ * Frequent subgraph mining (Sec. 2.1 "FSM"; Sec. 3.3 Listing 5).  In a
+ * vertex-labelled graph, an edge-induced embedding is a connected set of l
+ * edges; its pattern is the labelled graph formed by those edges and their
+ * endpoints (Sec. 2.1, edge-induced embeddings), up to label-preserving
+ * isomorphism.  The support of a pattern is its MNI (domain) support
+ * (Sec. 2.1): for every vertex of the pattern, the number of distinct graph
+ * vertices mapped to it over all embeddings of the pattern -- every
+ * matching, so an embedding contributes its vertices at every position an
+ * automorphism of the pattern can move them to -- and the support is the
+ * minimum over the pattern's vertices.  A pattern is frequent if its
+ * support is at least `min_support`.
+ *
+ * The oracle enumerates every connected edge set of 1 .. max_edges (<= 3)
+ * edges exactly once by its shape (a connected graph with at most 3 edges
+ * is an edge, a 2-edge path, a triangle, a 3-edge path or a 3-star) and
+ * computes the support of every pattern without filtering: the Filter
+ * phase of the method drops only embeddings of infrequent patterns, whose
+ * super-patterns are infrequent by the anti-monotonicity of MNI support,
+ * so the set of frequent patterns and their supports do not depend on it.
+ *
+ * Pattern format of this file's output: nv vertices (2..4), labels
+ * lab[0..nv) and adjacency bits over the pairs (0,1), (0,2), (0,3), (1,2),
+ * (1,3), (2,3) (bit index in that order), all in the canonical vertex
+ * order: the order that makes the tuple (lab[0], .., lab[nv-1], adjacency
+ * bits) lexicographically smallest.  Labels must be below 2^12.
+ */
+typedef struct {
+  int nv;
+  int lab[4];
+  unsigned adj;
+} fsm_pat;
+
+static int fsm_pb(int i, int j) { /* bit of the pair (i, j), i < j <= 3 */
+  return i == 0 ? j - 1 : (i == 1 ? j + 1 : 5);
+}
+static int fsm_adjacent(unsigned adj, int a, int b) {
+  if (a == b) return 0;
+  return a < b ? (adj >> fsm_pb(a, b)) & 1u : (adj >> fsm_pb(b, a)) & 1u;
+}
+
+static int fsm_perm[5][24][4];
+static int fsm_nperm[5];
+static int fsm_perm_ready = 0;
+
+static void fsm_perm_gen(int nv, int depth, int *cur, int used) {
+  if (depth == nv) {
+    memcpy(fsm_perm[nv][fsm_nperm[nv]++], cur, sizeof(int) * 4);
+    return;
+  }
+  for (int v = 0; v < nv; v++)
+    if (!(used & (1 << v))) {
+      cur[depth] = v;
+      fsm_perm_gen(nv, depth + 1, cur, used | (1 << v));
+    }
+}
+
+static void fsm_perm_init(void) {
+  if (fsm_perm_ready) return;
+  for (int nv = 1; nv <= 4; nv++) {
+    int cur[4] = {0, 0, 0, 0};
+    fsm_nperm[nv] = 0;
+    fsm_perm_gen(nv, 0, cur, 0);
+  }
+  fsm_perm_ready = 1;
+}
+
+/* the pattern seen through the vertex order p (position i = vertex p[i]) */
+static void fsm_reorder(const fsm_pat *in, const int *p, fsm_pat *out) {
+  out->nv = in->nv;
+  out->adj = 0;
+  for (int i = 0; i < 4; i++) out->lab[i] = i < in->nv ? in->lab[p[i]] : 0;
+  for (int i = 0; i < in->nv; i++)
+    for (int j = i + 1; j < in->nv; j++)
+      if (fsm_adjacent(in->adj, p[i], p[j])) out->adj |= 1u << fsm_pb(i, j);
+}
+
+static int fsm_cmp(const fsm_pat *x, const fsm_pat *y) {
+  if (x->nv != y->nv) return x->nv < y->nv ? -1 : 1;
+  for (int i = 0; i < x->nv; i++)
+    if (x->lab[i] != y->lab[i]) return x->lab[i] < y->lab[i] ? -1 : 1;
+  if (x->adj != y->adj) return x->adj < y->adj ? -1 : 1;
+  return 0;
+}
+
+/* canonical form of `in` and the order that produces it */
+static void fsm_canon(const fsm_pat *in, fsm_pat *out, int *best) {
+  fsm_pat cand;
+  for (int q = 0; q < fsm_nperm[in->nv]; q++) {
+    const int *p = fsm_perm[in->nv][q];
+    fsm_reorder(in, p, &cand);
+    if (q == 0 || fsm_cmp(&cand, out) < 0) {
+      *out = cand;
+      memcpy(best, p, sizeof(int) * 4);
+    }
+  }
+}
+
+/* orbit of every position of a canonical pattern under its automorphisms
+ * (orders that reproduce the same labels and adjacency): the smallest
+ * position an automorphism maps it to */
+static void fsm_orbits(const fsm_pat *c, int *orb) {
+  for (int i = 0; i < c->nv; i++) orb[i] = i;
+  fsm_pat img;
+  for (int q = 0; q < fsm_nperm[c->nv]; q++) {
+    const int *p = fsm_perm[c->nv][q];
+    fsm_reorder(c, p, &img);
+    if (fsm_cmp(&img, c) != 0) continue;
+    for (int i = 0; i < c->nv; i++)
+      if (p[i] < orb[i]) orb[i] = p[i];
+  }
+}
+
+typedef struct {
+  /* pattern table (open addressing on a packed key) */
+  uint64_t *keys;  /* packed key + 1, 0 = empty */
+  int32_t *slot;
+  int cap_log2;
+  fsm_pat *pats;
+  int *orb;        /* 4 per pattern */
+  uint64_t *count;
+  int npat, pat_cap;
+  /* (pattern, orbit, vertex) triples of every embedding and position */
+  uint64_t *tri;
+  int64_t ntri, tri_cap;
+  int err;
+} fsm_ctx;
+
+static uint64_t fsm_pack(const fsm_pat *c, int edges) {
+  uint64_t k = (uint64_t)edges | ((uint64_t)c->nv << 2) | ((uint64_t)c->adj << 5);
+  for (int i = 0; i < 4; i++) k |= (uint64_t)(i < c->nv ? c->lab[i] : 0) << (11 + 12 * i);
+  return k;
+}
+
+static int fsm_lookup(fsm_ctx *x, const fsm_pat *c, int edges) {
+  const uint64_t key = fsm_pack(c, edges) + 1;
+  const uint64_t mask = ((uint64_t)1 << x->cap_log2) - 1;
+  uint64_t h = (key * 0x9E3779B97F4A7C15ull) >> (64 - x->cap_log2);
+  for (;;) {
+    if (x->keys[h] == key) return x->slot[h];
+    if (x->keys[h] == 0) break;
+    h = (h + 1) & mask;
+  }
+  if (x->npat >= x->pat_cap) {
+    x->err = ORC_ENOMEM;
+    return -1;
+  }
+  const int id = x->npat++;
+  x->keys[h] = key;
+  x->slot[h] = id;
+  x->pats[id] = *c;
+  x->count[id] = 0;
+  fsm_orbits(c, x->orb + 4 * id);
+  return id;
+}
+
+/* one embedding: vertices v[0..nv) and adjacency over them */
+static void fsm_embedding(fsm_ctx *x, int nv, const int32_t *v, unsigned adj, const int32_t *lab) {
+  if (x->err) return;
+  fsm_pat e, c;
+  int best[4];
+  e.nv = nv;
+  e.adj = adj;
+  for (int i = 0; i < 4; i++) e.lab[i] = i < nv ? lab[v[i]] : 0;
+  fsm_canon(&e, &c, best);
+  int edges = 0;
+  for (int b = 0; b < 6; b++) edges += (adj >> b) & 1u;
+  const int id = fsm_lookup(x, &c, edges);
+  if (id < 0) return;
+  x->count[id]++;
+  if (x->ntri + nv > x->tri_cap) {
+    int64_t nc = x->tri_cap * 2 + 1024;
+    uint64_t *t = (uint64_t *)realloc(x->tri, (size_t)nc * sizeof(uint64_t));
+    if (!t) {
+      x->err = ORC_ENOMEM;
+      return;
+    }
+    x->tri = t;
+    x->tri_cap = nc;
+  }
+  for (int i = 0; i < nv; i++)  /* canonical position i holds vertex v[best[i]] */
+    x->tri[x->ntri++] = ((uint64_t)id << 36) | ((uint64_t)x->orb[4 * id + i] << 32) | (uint32_t)v[best[i]];
+}
+
+typedef struct {
+  int edges;
+  fsm_pat pat;
+  uint64_t support, count;
+} fsm_out;
+
+static int fsm_out_cmp(const void *a, const void *b) {
+  const fsm_out *x = (const fsm_out *)a, *y = (const fsm_out *)b;
+  if (x->edges != y->edges) return x->edges < y->edges ? -1 : 1;
+  return fsm_cmp(&x->pat, &y->pat);
+}
+
+static int cmp_u64(const void *a, const void *b) {
+  const uint64_t x = *(const uint64_t *)a, y = *(const uint64_t *)b;
+  return x < y ? -1 : (x > y ? 1 : 0);
+}
+
+/* Frequent patterns of 1 .. max_edges edges (max_edges in 1..3) with MNI
+ * support >= min_support (0 lists every pattern that occurs), ordered by
+ * (edges, nv, labels, adjacency).  Per pattern: meta[7] = (edges, nv, lab0,
+ * lab1, lab2, lab3, adjacency bits) and val[2] = (support, embeddings).
+ * *n_out receives the number of such patterns; at most `cap` are written. */
+int orc_fsm(int32_t n, const int64_t *rp, const int32_t *col, const int32_t *lab, int32_t max_edges,
+            int64_t min_support, int32_t *meta, uint64_t *val, int32_t cap, int32_t *n_out) {
+  if (n < 0 || max_edges < 1 || max_edges > 3 || !n_out) return ORC_EINVAL;
+  for (int32_t v = 0; v < n; v++)
+    if (lab[v] < 0 || lab[v] >= 4096) return ORC_EINVAL;
+  fsm_perm_init();
+  fsm_ctx x;
+  memset(&x, 0, sizeof(x));
+  x.cap_log2 = 18;
+  x.pat_cap = 1 << 17;
+  x.keys = (uint64_t *)calloc((size_t)1 << x.cap_log2, sizeof(uint64_t));
+  x.slot = (int32_t *)calloc((size_t)1 << x.cap_log2, sizeof(int32_t));
+  x.pats = (fsm_pat *)calloc((size_t)x.pat_cap, sizeof(fsm_pat));
+  x.orb = (int *)calloc((size_t)x.pat_cap * 4, sizeof(int));
+  x.count = (uint64_t *)calloc((size_t)x.pat_cap, sizeof(uint64_t));
+  int rc = ORC_OK;
+  if (!x.keys || !x.slot || !x.pats || !x.orb || !x.count) {
+    rc = ORC_ENOMEM;
+    goto done;
+  }
+  for (int32_t u = 0; u < n; u++) {
+    const int32_t *N = col + rp[u];
+    const int64_t d = rp[u + 1] - rp[u];
+    for (int64_t i = 0; i < d; i++) {
+      /* 1 edge: (u, N[i]) once, from its smaller end */
+      if (N[i] > u) {
+        int32_t v[4] = {u, N[i], 0, 0};
+        fsm_embedding(&x, 2, v, 1u << fsm_pb(0, 1), lab);
+      }
+      if (max_edges < 2) continue;
+      for (int64_t j = i + 1; j < d; j++) {
+        /* 2 edges: the pair at its shared vertex u */
+        int32_t v[4] = {u, N[i], N[j], 0};
+        fsm_embedding(&x, 3, v, (1u << fsm_pb(0, 1)) | (1u << fsm_pb(0, 2)), lab);
+        if (max_edges < 3) continue;
+        /* 3 edges, star: the triple at its centre u */
+        for (int64_t l = j + 1; l < d; l++) {
+          int32_t w[4] = {u, N[i], N[j], N[l]};
+          fsm_embedding(&x, 4, w, (1u << fsm_pb(0, 1)) | (1u << fsm_pb(0, 2)) | (1u << fsm_pb(0, 3)), lab);
+        }
+        /* 3 edges, triangle: once, from its smallest vertex */
+        if (N[i] > u && adjacent(rp, col, N[i], N[j])) {
+          int32_t w[4] = {u, N[i], N[j], 0};
+          fsm_embedding(&x, 3, w, (1u << fsm_pb(0, 1)) | (1u << fsm_pb(0, 2)) | (1u << fsm_pb(1, 2)), lab);
+        }
+      }
+      /* 3 edges, path a - u - c - b: once, from its middle edge (u, c), u < c */
+      const int32_t c = N[i];
+      if (max_edges < 3 || c < u) continue;
+      for (int64_t j = 0; j < d; j++) {
+        const int32_t a = N[j];
+        if (a == c) continue;
+        for (int64_t l = rp[c]; l < rp[c + 1]; l++) {
+          const int32_t b = col[l];
+          if (b == u || b == a) continue;
+          int32_t w[4] = {a, u, c, b};
+          fsm_embedding(&x, 4, w, (1u << fsm_pb(0, 1)) | (1u << fsm_pb(1, 2)) | (1u << fsm_pb(2, 3)), lab);
+        }
+      }
+    }
+    if (x.err) break;
+  }
+  if (x.err) {
+    rc = x.err;
+    goto done;
+  }
+  /* domains: the distinct (pattern, orbit, vertex) triples, counted per (pattern, orbit) */
+  qsort(x.tri, (size_t)x.ntri, sizeof(uint64_t), cmp_u64);
+  {
+    uint64_t *dom = (uint64_t *)calloc((size_t)x.npat * 4 + 1, sizeof(uint64_t));
+    fsm_out *res = (fsm_out *)malloc(sizeof(fsm_out) * (size_t)(x.npat + 1));
+    if (!dom || !res) {
+      free(dom);
+      free(res);
+      rc = ORC_ENOMEM;
+      goto done;
+    }
+    for (int64_t t = 0; t < x.ntri; t++)
+      if (t == 0 || x.tri[t] != x.tri[t - 1]) dom[(x.tri[t] >> 36) * 4 + ((x.tri[t] >> 32) & 15)]++;
+    int32_t nr = 0;
+    for (int32_t q = 0; q < x.npat; q++) {
+      uint64_t sup = UINT64_MAX; /* the smallest domain over the pattern's vertices */
+      for (int i = 0; i < x.pats[q].nv; i++) {
+        const uint64_t d = dom[(uint64_t)q * 4 + (uint64_t)x.orb[4 * q + i]];
+        if (d < sup) sup = d;
+      }
+      if ((int64_t)sup < min_support) continue;
+      int edges = 0;
+      for (int bit = 0; bit < 6; bit++) edges += (x.pats[q].adj >> bit) & 1u;
+      res[nr].edges = edges;
+      res[nr].pat = x.pats[q];
+      res[nr].support = sup;
+      res[nr].count = x.count[q];
+      nr++;
+    }
+    qsort(res, (size_t)nr, sizeof(fsm_out), fsm_out_cmp);
+    for (int32_t r = 0; r < nr && r < cap; r++) {
+      int32_t *m = meta + 7 * (int64_t)r;
+      m[0] = res[r].edges;
+      m[1] = res[r].pat.nv;
+      for (int i = 0; i < 4; i++) m[2 + i] = i < res[r].pat.nv ? res[r].pat.lab[i] : 0;
+      m[6] = (int32_t)res[r].pat.adj;
+      val[2 * (int64_t)r] = res[r].support;
+      val[2 * (int64_t)r + 1] = res[r].count;
+    }
+    *n_out = nr;
+    free(res);
+    free(dom);
+  }
+done:
+  free(x.keys);
+  free(x.slot);
+  free(x.pats);
+  free(x.orb);
+  free(x.count);
+  free(x.tri);
+  return rc;
+}
+
+/* MNI support by its textbook definition, for pins on tiny graphs (n <= 64):
+ * every injective map f of the pattern's vertices (nv <= 4, labels plab,
+ * adjacency bits padj in the pair order above) into the graph that keeps
+ * labels and maps every pattern edge onto a graph edge (edge-induced: other
+ * graph edges among the images are allowed); the domain of pattern vertex i
+ * is the set of f(i); support = the smallest domain.  *matchings receives
+ * the number of such maps (= embeddings x automorphisms). */
+int orc_fsm_bf_support(int32_t n, const int64_t *rp, const int32_t *col, const int32_t *lab, int32_t nv,
+                       const int32_t *plab, int32_t padj, uint64_t *support, uint64_t *matchings) {
+  if (n < 0 || n > 64 || nv < 1 || nv > 4 || !support || !matchings) return ORC_EINVAL;
+  if (n == 0) {
+    *support = 0;
+    *matchings = 0;
+    return ORC_OK;
+  }
+  uint64_t adj[64];
+  bits_from_csr(n, rp, col, adj);
+  uint64_t dom[4] = {0, 0, 0, 0};
+  uint64_t cnt = 0;
+  int32_t f[4] = {0, 0, 0, 0};
+  /* odometer over all nv-tuples of vertices */
+  for (;;) {
+    int ok = 1;
+    for (int i = 0; i < nv && ok; i++) {
+      if (lab[f[i]] != plab[i]) ok = 0;
+      for (int j = 0; j < i && ok; j++) {
+        if (f[i] == f[j]) ok = 0;
+        else if (fsm_adjacent((unsigned)padj, j, i) && !((adj[f[i]] >> f[j]) & 1u)) ok = 0;
+      }
+    }
+    if (ok) {
+      cnt++;
+      for (int i = 0; i < nv; i++) dom[i] |= 1ull << f[i];
+    }
+    int p = 0;
+    while (p < nv && ++f[p] == n) f[p++] = 0;
+    if (p == nv) break;
+  }
+  uint64_t s = UINT64_MAX;
+  for (int i = 0; i < nv; i++) {
+    const uint64_t d = (uint64_t)popcount64(dom[i]);
+    if (d < s) s = d;
+  }
+  *support = s;
+  *matchings = cnt;
+  return ORC_OK;
 }
