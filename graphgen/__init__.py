@@ -318,3 +318,31 @@ def rmat_weak(scale: int, seed: int = 1) -> CSR:
     """R-MAT of the weak-scaling series: 2^scale vertices, average degree 20
     (10 * 2^scale undirected edges), same (a, b, c, d) as the R-MAT workload."""
     return _cached(f"rmat{scale}_d20_s{seed}", lambda: rmat(1 << scale, 10 << scale, RMAT_ABC, seed))
+
+
+# ------------------------------------------------------------ vertex labels
+def vertex_labels(n: int, nlabels: int, seed: int = 1, skew: float = 0.0) -> np.ndarray:
+    """Seeded vertex labels in [0, nlabels) (int32[n]): uniform, or with
+    P(label i) proportional to (i + 1)^-skew -- the uneven label frequencies
+    of the labelled graphs that frequent subgraph mining runs on."""
+    rng = np.random.default_rng(seed)
+    if skew <= 0.0:
+        return rng.integers(0, nlabels, size=n).astype(np.int32)
+    p = (np.arange(1, nlabels + 1, dtype=np.float64)) ** -skew
+    return rng.choice(nlabels, size=n, p=p / p.sum()).astype(np.int32)
+
+
+def mico_like(seed: int = 1) -> CSR:
+    """Stand-in for the paper's Mico input (Table 1: 100,000 vertices,
+    2,160,312 arcs, average degree 22, 29 labels): Chung-Lu, n = 100,000,
+    exponent 2.1, mean weight 21.6, weights capped at 1,359; its labels are
+    vertex_labels(n, 29, seed, skew=1.0)."""
+    return _cached(f"micolike_s{seed}", lambda: chung_lu(100_000, 2.1, 21.6, 1359.0, seed))
+
+
+def patent_like(seed: int = 1) -> CSR:
+    """Stand-in for the paper's Patents input (Table 1: 2,745,761 vertices,
+    27,930,818 arcs, average degree 10, 37 labels): Chung-Lu, n = 2,745,761,
+    exponent 2.5, mean weight 10.2, weights capped at 800; its labels are
+    vertex_labels(n, 37, seed, skew=1.0)."""
+    return _cached(f"patentlike_s{seed}", lambda: chung_lu(2_745_761, 2.5, 10.2, 800.0, seed))

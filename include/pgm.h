@@ -379,6 +379,46 @@ pgm_status pgm_count_triangles_noalloc(int32_t n, const int32_t *dag_rowptr_dev,
                                        const int32_t *dag_col_dev, int64_t m,
                                        unsigned long long *count_dev, void *stream);
 
+/* ------------------------------------------- frequent subgraph mining */
+
+/* Vertex labels for pgm_fsm: labels is a HOST array int32[n], each label in
+ * [0, 2^15); copied to the device (the caller keeps ownership).  Replaces
+ * earlier labels.  PGM_EINVAL on a null array (n > 0) or a label out of
+ * range (nothing changed then). */
+pgm_status pgm_graph_set_labels(pgm_graph *g, const int32_t *labels);
+
+/* One frequent pattern: its vertices in canonical order -- the order that
+ * makes (labels[0..nv-1], adj) lexicographically smallest, adj bit i set
+ * when pair i of (0,1),(0,2),(0,3),(1,2),(1,3),(2,3) is an edge -- its MNI
+ * support and its number of edge-induced embeddings (distinct edge sets). */
+typedef struct pgm_fsm_pattern {
+  int32_t edges;       /* 1, 2 or 3 */
+  int32_t nv;          /* vertices: 2, 3 or 4 */
+  int32_t labels[4];   /* labels[nv..3] = 0 */
+  uint32_t adj;
+  uint32_t pad;
+  uint64_t support;    /* smallest domain over the pattern's vertices */
+  uint64_t embeddings;
+} pgm_fsm_pattern;
+
+/* Frequent subgraph mining (Sec. 2.1 "FSM"; Sec. 3.3 Listing 5): the
+ * connected labelled patterns of 1..max_edges edges (max_edges = 1, 2 or 3)
+ * whose minimum-image-based support -- over the orbits of the pattern, the
+ * smallest number of distinct graph vertices that play that orbit in some
+ * edge-induced embedding -- is at least min_support (>= 1).  Embeddings are
+ * extended one edge at a time, only from frequent patterns (Filter).
+ * Labels come from pgm_graph_set_labels (PGM_EINVAL without).  out is a
+ * HOST array of cap patterns, written in the order (edges, nv, labels, adj);
+ * out = NULL (cap 0) is a size query; *n_out receives the number of
+ * frequent patterns, and PGM_EOVERFLOW (nothing written) when it exceeds
+ * cap.  Device memory: a 2^22-slot pattern table per level (PGM_ENOMEM when
+ * the distinct patterns of one size overfill it) and 4 * ceil(n / 32) words
+ * of domain bitmap per pattern whose embedding count leaves it a chance to
+ * be frequent, in passes over the level of at most 64 GB of bitmaps (or 60%
+ * of the free device memory).  Other max_edges: PGM_EUNSUPPORTED. */
+pgm_status pgm_fsm(pgm_graph *g, int32_t max_edges, int64_t min_support, pgm_fsm_pattern *out, int32_t cap,
+                   int32_t *n_out);
+
 /* ---------------------------------------------------------------- misc */
 
 pgm_status pgm_set_options(const pgm_options *o);

@@ -225,6 +225,7 @@ void Workspace::release_all() {
   scan_tmp.release();
   scratch.release();
   tri.release();
+  dom.release();
 }
 
 }  // namespace pgm

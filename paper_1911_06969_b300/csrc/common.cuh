@@ -123,6 +123,7 @@ struct Workspace {
   DevArr<int64_t> scan_tmp;          // block partials of the scan
   DevArr<int32_t> scratch;           // per-warp spill lists of the hub kernels
   DevArr<uint2> tri;                 // motifs: per-arc triangle counts of the level-2 edges
+  DevArr<uint32_t> dom;              // frequent subgraph mining: domain bitmaps
   void release_all();
 };
 
@@ -140,6 +141,9 @@ struct Graph {
   int32_t* gid = nullptr;      // batches: vertex -> graph id (nullptr otherwise)
   int32_t* src = nullptr;      // motifs: source vertex of every arc
   int32_t* rev = nullptr;      // motifs: index of the reverse arc (v -> u) of every arc u -> v
+  int32_t* labels = nullptr;   // frequent subgraph mining: vertex labels (pgm_graph_set_labels)
+  int32_t* label_rank = nullptr;       // vertex -> its index among the vertices of its label
+  std::vector<int64_t> h_label_count;  // vertices per label
   int32_t* hub_idx = nullptr;  // motifs: vertex -> row of hub_bits, or -1
   uint32_t* hub_bits = nullptr;  // motifs: adjacency bitmaps of the highest-degree vertices
   int64_t hub_words = 0;       // 32-bit words per bitmap row

@@ -224,9 +224,14 @@ void graph_free(Graph& g) {
   if (g.src) cudaFree(g.src);
   if (g.rev) cudaFree(g.rev);
   if (g.hub_idx) cudaFree(g.hub_idx);
+  if (g.labels) cudaFree(g.labels);
+  if (g.label_rank) cudaFree(g.label_rank);
   if (g.hub_bits) cudaFree(g.hub_bits);
   g.rp = g.col = g.dag_rp = g.dag_col = g.gid = g.up = g.src = g.hub_idx = g.rev = nullptr;
   g.hub_bits = nullptr;
+  g.labels = nullptr;
+  g.label_rank = nullptr;
+  g.h_label_count.clear();
   g.nhubs = 0;
   g.ws.release_all();
   g.oriented = false;

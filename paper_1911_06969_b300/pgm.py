@@ -93,6 +93,11 @@ class pgm_result(C.Structure):
                 ("start_s", C.c_double), ("finish_s", C.c_double), ("mem_bytes", C.c_int64)]
 
 
+class pgm_fsm_pattern(C.Structure):
+    _fields_ = [("edges", C.c_int32), ("nv", C.c_int32), ("labels", C.c_int32 * 4), ("adj", C.c_uint32),
+                ("pad", C.c_uint32), ("support", C.c_uint64), ("embeddings", C.c_uint64)]
+
+
 P = C.c_void_p
 _SIGS = {
     "pgm_graph_create_csr": (C.c_int, [C.c_int32, P, P, C.c_uint32, P, C.POINTER(P)]),
@@ -133,6 +138,8 @@ _SIGS = {
     "pgm_kernel_launches": (C.c_uint64, []),
     "pgm_debug_errors": (C.c_uint64, [C.c_int32]),
     "pgm_count_triangles_noalloc": (C.c_int, [C.c_int32, P, P, C.c_int64, P, P]),
+    "pgm_graph_set_labels": (C.c_int, [P, P]),
+    "pgm_fsm": (C.c_int, [P, C.c_int32, C.c_int64, C.POINTER(pgm_fsm_pattern), C.c_int32, C.POINTER(C.c_int32)]),
 }
 
 _lib = None
@@ -266,6 +273,24 @@ def pgm_list_motifs_host(g: int, k: int, out=None) -> int:
         _ok(load().pgm_list_motifs_host(g, k, out.ctypes.data, out.size // (k + 1), C.byref(n)),
             "pgm_list_motifs_host")
     return int(n.value)
+
+
+def pgm_graph_set_labels(g: int, labels) -> None:
+    """Vertex labels (int32 per vertex, each in [0, 2^15)) for pgm_fsm."""
+    lab = np.ascontiguousarray(labels, dtype=np.int32)
+    _ok(load().pgm_graph_set_labels(g, lab.ctypes.data if lab.size else None), "pgm_graph_set_labels")
+
+
+def pgm_fsm(g: int, max_edges: int, min_support: int = 1) -> list:
+    """Frequent labelled patterns of 1..max_edges edges with MNI support >=
+    min_support, as dicts {edges, labels (canonical order, tuple of nv),
+    adj, support, embeddings} in the order (edges, nv, labels, adj)."""
+    n = C.c_int32()
+    _ok(load().pgm_fsm(g, max_edges, min_support, None, 0, C.byref(n)), "pgm_fsm")
+    buf = (pgm_fsm_pattern * max(n.value, 1))()
+    _ok(load().pgm_fsm(g, max_edges, min_support, buf, n.value, C.byref(n)), "pgm_fsm")
+    return [{"edges": p.edges, "labels": tuple(p.labels[:p.nv]), "adj": int(p.adj), "support": int(p.support),
+             "embeddings": int(p.embeddings)} for p in buf[:n.value]]
 
 
 def _npat(k: int) -> int:
@@ -459,6 +484,13 @@ class Graph:
 
     def stats(self) -> dict:
         return pgm_graph_stats_get(self.h)
+
+    def set_labels(self, labels):
+        pgm_graph_set_labels(self.h, labels)
+        return self
+
+    def fsm(self, max_edges: int, min_support: int = 1) -> list:
+        return pgm_fsm(self.h, max_edges, min_support)
 
     def close(self):
         if self.h:
