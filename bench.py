@@ -251,6 +251,10 @@ def main(argv=None):
                     help="profiling: time only motif counting (--motif-k) on a graph of N vertices")
     ap.add_argument("--motif-k", type=int, default=4, choices=[3, 4, 5],
                     help="profiling: motif size of --motif-only (3, 4: Chung-Lu graph; 5: G(N, 10/(N-1)))")
+    ap.add_argument("--fsm-only", default="", choices=["", "mico_like", "patent_like"],
+                    help="profiling: time only frequent subgraph mining on this labelled stand-in")
+    ap.add_argument("--fsm-edges", type=int, default=2, help="profiling: pattern edges of --fsm-only (3-FSM = 2)")
+    ap.add_argument("--fsm-support", type=int, default=300, help="profiling: min_support of --fsm-only")
     ap.add_argument("--sweep", action="store_true", help="R-MAT weak-scaling series (average degree 20)")
     ap.add_argument("--sweep-scales", default="20,21,22,23,24,25")
     args = ap.parse_args(argv)
@@ -258,6 +262,8 @@ def main(argv=None):
         return run_reference(args)
     if args.motif_only:
         return motif_only(args)
+    if args.fsm_only:
+        return fsm_only(args)
     if args.sweep:
         return sweep(args)
 
@@ -609,6 +615,74 @@ def extras(pgm, torch, stream, flush):
     out["serving_64_graphs"] = serving(pgm)
     out["listing_triangles_rmat21"] = listing(pgm, torch)
     out["motif5_ba20k"] = motif5(pgm)
+    out["fsm"] = fsm(pgm, torch)
+    return out
+
+
+def fsm_only(args):
+    """One labelled stand-in, `--warmup` untimed and `--steps` timed FSM calls."""
+    import torch
+
+    from paper_1911_06969_b300 import pgm
+
+    make, nlab = {"mico_like": (gg.mico_like, 29), "patent_like": (gg.patent_like, 37)}[args.fsm_only]
+    g = make()
+    with pgm.Graph(g) as G:
+        G.set_labels(gg.vertex_labels(g.n, nlab, seed=1, skew=1.0))
+        for _ in range(args.warmup):
+            res = G.fsm(args.fsm_edges, args.fsm_support)
+        ts = []
+        for _ in range(args.steps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            res = G.fsm(args.fsm_edges, args.fsm_support)
+            ts.append(time.perf_counter() - t0)
+    print(json.dumps({"workload": f"{args.fsm_edges + 1}-FSM on {g.name}, {nlab} labels, "
+                                  f"min_support {args.fsm_support}", "ms": [round(t * 1e3, 3) for t in ts],
+                      "patterns": len(res)}), flush=True)
+    return 0
+
+
+def fsm_shape_totals(g):
+    """Edge-induced embeddings per shape from the degrees: m edges and
+    sum C(d, 2) two-edge paths (a check of the 3-FSM counts at min_support 1)."""
+    d = np.diff(np.asarray(g.rowptr)).astype(np.int64)
+    return {"1": g.m, "2": int((d * (d - 1) // 2).sum())}
+
+
+def fsm(pgm, torch):
+    """Frequent subgraph mining on the Mico and Patents stand-ins (29 / 37
+    skewed labels): 3-FSM (patterns of up to 2 edges) at the paper's
+    min_support values 300, 500, 1000, 5000, and 4-FSM (up to 3 edges) on
+    the Patents stand-in at 30K, 20K, 15K.  Wall time of the whole call
+    (host result assembly included; the call synchronises)."""
+    out = {}
+    for name, make, nlab in (("mico_like", gg.mico_like, 29), ("patent_like", gg.patent_like, 37)):
+        g = make()
+        lab = gg.vertex_labels(g.n, nlab, seed=1, skew=1.0)
+        rows = {}
+        with pgm.Graph(g) as G:
+            G.set_labels(lab)
+            full = G.fsm(2, 1)  # also the first call: arc helpers, bitmaps
+            sums = {"1": 0, "2": 0}
+            for p in full:
+                sums[str(p["edges"])] += p["embeddings"]
+            runs = [(2, s) for s in (300, 500, 1000, 5000)]
+            if name == "patent_like":
+                runs += [(3, s) for s in (30000, 20000, 15000)]
+            for me, sigma in runs:
+                ts = []
+                for _ in range(3 if me == 2 else 1):
+                    torch.cuda.synchronize()
+                    t0 = time.perf_counter()
+                    res = G.fsm(me, sigma)
+                    ts.append(time.perf_counter() - t0)
+                rows[f"{me + 1}-FSM sigma={sigma}"] = {
+                    "ms": min(ts) * 1e3, "patterns": len(res),
+                    "by_edges": [sum(1 for p in res if p["edges"] == e) for e in (1, 2, 3)],
+                    "subset_of_min_support_1": (res == [p for p in full if p["support"] >= sigma]) if me == 2 else None}
+        out[name] = {"graph": g.name, "n": g.n, "arcs": g.narcs, "labels": nlab, "runs": rows,
+                     "embeddings_match_closed_form": sums == fsm_shape_totals(g)}
     return out
 
 

@@ -409,13 +409,16 @@ typedef struct pgm_fsm_pattern {
  * extended one edge at a time, only from frequent patterns (Filter).
  * Labels come from pgm_graph_set_labels (PGM_EINVAL without).  out is a
  * HOST array of cap patterns, written in the order (edges, nv, labels, adj);
- * out = NULL (cap 0) is a size query; *n_out receives the number of
- * frequent patterns, and PGM_EOVERFLOW (nothing written) when it exceeds
- * cap.  Device memory: a 2^22-slot pattern table per level (PGM_ENOMEM when
- * the distinct patterns of one size overfill it) and 4 * ceil(n / 32) words
- * of domain bitmap per pattern whose embedding count leaves it a chance to
- * be frequent, in passes over the level of at most 64 GB of bitmaps (or 60%
- * of the free device memory).  Other max_edges: PGM_EUNSUPPORTED. */
+ * out = NULL (cap 0) is a size query, which runs the whole mining (a
+ * caller can pass a generous cap instead and retry on PGM_EOVERFLOW);
+ * *n_out receives the number of frequent patterns, and PGM_EOVERFLOW
+ * (nothing written) when it exceeds cap.  Device memory: a 2^22-slot
+ * pattern table per level (PGM_ENOMEM when the distinct patterns of one
+ * size overfill it) and, per pattern whose embedding count leaves it a
+ * chance to be frequent, one bitmap per orbit over the vertices of the
+ * orbit's label, in passes over the level of at most 64 GB of bitmaps (or
+ * 60% of the free device memory); the bitmaps stay with the handle for the
+ * next call.  Other max_edges: PGM_EUNSUPPORTED. */
 pgm_status pgm_fsm(pgm_graph *g, int32_t max_edges, int64_t min_support, pgm_fsm_pattern *out, int32_t cap,
                    int32_t *n_out);
 

@@ -286,9 +286,14 @@ def pgm_fsm(g: int, max_edges: int, min_support: int = 1) -> list:
     min_support, as dicts {edges, labels (canonical order, tuple of nv),
     adj, support, embeddings} in the order (edges, nv, labels, adj)."""
     n = C.c_int32()
-    _ok(load().pgm_fsm(g, max_edges, min_support, None, 0, C.byref(n)), "pgm_fsm")
-    buf = (pgm_fsm_pattern * max(n.value, 1))()
-    _ok(load().pgm_fsm(g, max_edges, min_support, buf, n.value, C.byref(n)), "pgm_fsm")
+    cap = 1 << 16  # one mining run unless the result is larger (then a second with the exact size)
+    buf = (pgm_fsm_pattern * cap)()
+    rc = load().pgm_fsm(g, max_edges, min_support, buf, cap, C.byref(n))
+    if rc == PGM_EOVERFLOW:
+        cap = n.value
+        buf = (pgm_fsm_pattern * cap)()
+        rc = load().pgm_fsm(g, max_edges, min_support, buf, cap, C.byref(n))
+    _ok(rc, "pgm_fsm")
     return [{"edges": p.edges, "labels": tuple(p.labels[:p.nv]), "adj": int(p.adj), "support": int(p.support),
              "embeddings": int(p.embeddings)} for p in buf[:n.value]]
 
