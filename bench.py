@@ -243,7 +243,7 @@ def main(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--scale", type=int, default=21, help="R-MAT scale (profiling runs use a smaller graph)")
     ap.add_argument("--edges", type=int, default=28_000_000, help="R-MAT undirected edges")
-    ap.add_argument("--k", type=int, default=4, choices=[3, 4, 5],
+    ap.add_argument("--k", type=int, default=4, choices=list(range(3, 11)),
                     help="clique size of the step (profiling runs; the benchmark is k = 4)")
     ap.add_argument("--clique-engine", type=int, default=0, choices=[0, 1, 2],
                     help="profiling: 0 auto, 1 level lists, 2 bitset levels")

@@ -391,6 +391,7 @@ extern "C" {
 
 pgm_status pgm_batch_create(int32_t G, const int64_t* vtx_off, const int64_t* rowptr_cat,
                             const int32_t* col_cat, uint32_t flags, void* stream, pgm_batch** out) {
+  PGM_NVTX("pgm_batch_create");
   if (!out || G < 0 || !vtx_off || !rowptr_cat) {
     pgm::set_error("pgm_batch_create: bad arguments");
     return PGM_EINVAL;
@@ -480,6 +481,7 @@ pgm_status pgm_batch_create(int32_t G, const int64_t* vtx_off, const int64_t* ro
 }
 
 pgm_status pgm_batch_count_motifs(pgm_batch* b, int32_t k, uint64_t* out, const pgm_tune* t) {
+  PGM_NVTX("pgm_batch_count_motifs");
   if (!b || !out) {
     pgm::set_error("pgm_batch_count_motifs: null argument");
     return PGM_EINVAL;
@@ -488,6 +490,7 @@ pgm_status pgm_batch_count_motifs(pgm_batch* b, int32_t k, uint64_t* out, const 
 }
 
 pgm_status pgm_batch_count_kcliques(pgm_batch* b, int32_t k, uint64_t* out, const pgm_tune* t) {
+  PGM_NVTX("pgm_batch_count_kcliques");
   if (!b || !out) {
     pgm::set_error("pgm_batch_count_kcliques: null argument");
     return PGM_EINVAL;
@@ -496,6 +499,7 @@ pgm_status pgm_batch_count_kcliques(pgm_batch* b, int32_t k, uint64_t* out, cons
 }
 
 pgm_status pgm_batch_count_motifs_loop(pgm_batch* b, int32_t k, uint64_t* out) {
+  PGM_NVTX("pgm_batch_count_motifs_loop");
   if (!b || !out) {
     pgm::set_error("pgm_batch_count_motifs_loop: null argument");
     return PGM_EINVAL;
@@ -534,6 +538,7 @@ pgm_status pgm_batch_autotune(pgm_batch* b, int32_t k, pgm_tune* best, double* b
 
 pgm_status pgm_batch_autotune_ex(pgm_batch* b, int32_t k, const char* cache_path, pgm_tune* best, double* best_ms,
                                  pgm_tune_trial* trials, int32_t cap, int32_t* n_trials, int32_t* from_cache) {
+  PGM_NVTX("pgm_batch_autotune_ex");
   if (!b || !best || !best_ms || cap < 0 || (cap > 0 && !trials)) {
     pgm::set_error("pgm_batch_autotune: bad arguments");
     return PGM_EINVAL;

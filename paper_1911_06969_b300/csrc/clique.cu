@@ -258,6 +258,7 @@ struct CliqueRun {
   }
 
   pgm_status level(int l, const Lvl& L) {
+    PGM_NVTX(kNvtxLevel[l < 13 ? l : 12]);
     chain[l] = L;
     const int64_t E = L.e_hi - L.e_lo;
     const int64_t P = L.p_hi - L.p_lo;
@@ -518,6 +519,7 @@ pgm_status count_kcliques(Graph& g, Workspace& ws, cudaStream_t s, int k, int32_
 extern "C" {
 
 pgm_status pgm_count_kcliques(pgm_graph* g, int32_t k, uint64_t* out_count) {
+  PGM_NVTX("pgm_count_kcliques");
   if (!g || !out_count) {
     pgm::set_error("pgm_count_kcliques: null argument");
     return PGM_EINVAL;
@@ -531,6 +533,7 @@ pgm_status pgm_count_kcliques(pgm_graph* g, int32_t k, uint64_t* out_count) {
 
 pgm_status pgm_count_kcliques_range(pgm_graph* g, int32_t k, int32_t v_lo, int32_t v_hi,
                                     uint64_t* out_count) {
+  PGM_NVTX("pgm_count_kcliques_range");
   if (!g || !out_count) {
     pgm::set_error("pgm_count_kcliques_range: null argument");
     return PGM_EINVAL;
@@ -605,10 +608,12 @@ static pgm_status list_kcliques_to(pgm_graph* g, int32_t k, int32_t* out, int64_
 }
 
 pgm_status pgm_list_kcliques(pgm_graph* g, int32_t k, int32_t* out_dev, int64_t cap_rows, int64_t* n_rows) {
+  PGM_NVTX("pgm_list_kcliques");
   return list_kcliques_to(g, k, out_dev, cap_rows, n_rows, false, "pgm_list_kcliques");
 }
 
 pgm_status pgm_list_kcliques_host(pgm_graph* g, int32_t k, int32_t* out_host, int64_t cap_rows, int64_t* n_rows) {
+  PGM_NVTX("pgm_list_kcliques_host");
   return list_kcliques_to(g, k, out_host, cap_rows, n_rows, true, "pgm_list_kcliques_host");
 }
 

@@ -14,6 +14,8 @@
 #include <mutex>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/pgm.h"
 
 namespace pgm {
@@ -46,6 +48,22 @@ void note_launches(uint64_t n);
     ::pgm::note_launches(1);            \
     PGM_TRY_CUDA(cudaGetLastError());   \
   } while (0)
+
+// NVTX range over a scope: every public counting, listing, mining and
+// batch call (and each level of the level-wise engines) appears as a named
+// range in Nsight Systems; without a tool attached a push/pop is a no-op.
+struct NvtxScope {
+  explicit NvtxScope(const char* name) { nvtxRangePushA(name); }
+  ~NvtxScope() { nvtxRangePop(); }
+  NvtxScope(const NvtxScope&) = delete;
+  NvtxScope& operator=(const NvtxScope&) = delete;
+};
+#define PGM_NVTX_CAT2(a, b) a##b
+#define PGM_NVTX_CAT(a, b) PGM_NVTX_CAT2(a, b)
+#define PGM_NVTX(name) ::pgm::NvtxScope PGM_NVTX_CAT(nvtx_scope_, __LINE__)(name)
+// names of the level ranges of the level-wise engines
+constexpr const char* kNvtxLevel[13] = {"level 0", "level 1", "level 2",  "level 3",  "level 4",  "level 5", "level 6",
+                                        "level 7", "level 8", "level 9", "level 10", "level 11", "level 12"};
 
 // ----------------------------------------------------------------- options
 pgm_options& options();  // current options (defaults filled); read-only while counting

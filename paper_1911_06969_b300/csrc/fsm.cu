@@ -43,10 +43,17 @@ constexpr int64_t kFsmDomainBytes = (int64_t)64 << 30;  // domain bitmaps held a
 
 enum FsmType : int { fEdge = 1, fWedge = 2, fTriangle = 3, fStar = 4, fPath = 5 };
 
+// The pattern table of a level, open addressing on the key.  Per slot: the
+// key, the compact ID of a pattern that may be frequent (else -1), its
+// Filter flag (set once the level's supports are known) and, during a
+// domain pass, the first word of each orbit's domain row (off.x = -1: the
+// pattern is not in this pass) -- one 16-byte load after the probe.
 struct FsmTable {
   unsigned long long* keys;  // 0 = empty
-  int32_t* id;               // compact ID of a pattern that may be frequent, else -1
-  unsigned long long* cnt;   // embeddings per slot (first pass)
+  int32_t* id;
+  uint8_t* frequent;
+  int4* off;
+  unsigned long long* cnt;  // embeddings per slot (first pass)
   uint32_t mask;
 };
 
@@ -91,10 +98,10 @@ __device__ __forceinline__ int fsm_slot(const FsmTable& T, unsigned long long k)
   return -1;
 }
 
-// compact ID of a key, -1 if absent or ruled out
-__device__ __forceinline__ int fsm_find(const FsmTable& T, unsigned long long k) {
+// the pattern of a key is known to be frequent
+__device__ __forceinline__ bool fsm_frequent(const FsmTable& T, unsigned long long k) {
   const int h = fsm_slot(T, k);
-  return h >= 0 ? T.id[h] : -1;
+  return h >= 0 && T.frequent[h] != 0;
 }
 
 struct FsmArgs {
@@ -107,12 +114,9 @@ struct FsmArgs {
   int64_t narcs;
   int mode;            // 0: insert and count pattern keys, 1: mark domains
   FsmTable T;          // this level's patterns
-  FsmTable T2;         // level 3: the 2-edge patterns
-  const uint8_t* freq2;     // level 3: 2-edge pattern ID -> frequent
+  FsmTable T2;         // level 3: the 2-edge patterns (frequent flags set)
   const uint8_t* freq_arc;  // levels 2, 3: the arc's 1-edge pattern is frequent
-  uint32_t* dom;            // mode 1: domain bitmaps of IDs [id_lo, id_lo + id_n)
-  const int64_t* rowoff;    // mode 1: first word of row (ID - id_lo) * 4 + orbit
-  int32_t id_lo, id_n;
+  uint32_t* dom;            // mode 1: domain bitmaps of this pass (rows at the slots' off[])
   unsigned long long* queue;  // work queue
   unsigned long long* err;    // [0] table full, [1] pattern missing in mode 1
   unsigned long long* stat;   // candidates examined
@@ -121,7 +125,8 @@ struct FsmArgs {
 // One embedding per lane (valid lanes only).  Mode 0: insert its key and
 // count it (one atomic per distinct pattern of the warp).  Mode 1: set its
 // vertices' bits in the domain bitmaps of their orbits, for the patterns
-// that kept an ID.
+// with rows in this pass; the bit positions (label ranks) are loaded before
+// the probe, so that they do not wait behind it.
 __device__ __forceinline__ void fsm_emit(const FsmArgs& A, bool valid, unsigned long long key, int nv,
                                          const int32_t (&v)[4], const int (&orb)[4]) {
   if (A.mode == 0) {
@@ -131,14 +136,22 @@ __device__ __forceinline__ void fsm_emit(const FsmArgs& A, bool valid, unsigned 
     if (h >= 0 && (int)(threadIdx.x & 31) == __ffs(grp) - 1) atomicAdd(A.T.cnt + h, (unsigned long long)__popc(grp));
     return;
   }
+  int32_t r[4] = {0, 0, 0, 0};  // bit positions, loaded before the probe (independent of it)
+#pragma unroll
+  for (int i = 0; i < 4; i++)
+    if (valid && i < nv) r[i] = A.rank[v[i]];
   const int h = valid ? fsm_slot(A.T, key) : -1;
   if (valid && h < 0) atomicAdd(A.err + 1, 1ull);
-  const int id = (h >= 0 ? A.T.id[h] : -1) - A.id_lo;
-  if (id >= 0 && id < A.id_n)
-    for (int i = 0; i < nv; i++) {
-      const int32_t r = A.rank[v[i]];
-      atomicOr(A.dom + A.rowoff[(int64_t)id * 4 + orb[i]] + (r >> 5), 1u << (r & 31));
-    }
+  const int4 e1 = h >= 0 ? A.T.off[h] : make_int4(-1, 0, 0, 0);
+  if (e1.x >= 0) {  // the pattern has rows in this pass
+#pragma unroll
+    for (int i = 0; i < 4; i++)
+      if (i < nv) {
+        const int o = orb[i];
+        const int32_t row = o == 0 ? e1.x : (o == 1 ? e1.y : (o == 2 ? e1.z : e1.w));
+        atomicOr(A.dom + row + (r[i] >> 5), 1u << (r[i] & 31));
+      }
+  }
 }
 
 // ---------------------------------------------------- pattern descriptions
@@ -335,8 +348,7 @@ __global__ void __launch_bounds__(256) fsm_level3(FsmArgs A) {
         if (pr.ok) {  // Filter: the 2-edge pattern must be frequent
           int32_t v[4];
           int orb[4];
-          const int id = fsm_find(A.T2, fsm_wedge(A.lab, pr.centre, pr.x, pr.y, v, orb));
-          pr.ok = id >= 0 && A.freq2[id];
+          pr.ok = fsm_frequent(A.T2, fsm_wedge(A.lab, pr.centre, pr.x, pr.y, v, orb));
         }
         for (unsigned todo = __ballot_sync(kFull, pr.ok); todo; todo &= todo - 1) {
           const int q = __ffs(todo) - 1;
@@ -400,6 +412,8 @@ __global__ void fsm_assign(FsmTable T, int64_t min_support, unsigned long long* 
     const unsigned long long k = T.keys[h];
     if (!k) continue;
     const unsigned long long c = T.cnt[h];
+    T.frequent[h] = 0;
+    T.off[h] = make_int4(-1, 0, 0, 0);
     if ((double)c * fsm_key_nv(k) >= (double)min_support) {
       const unsigned long long i = atomicAdd(nid, 1ull);
       T.id[h] = (int32_t)i;
@@ -408,6 +422,31 @@ __global__ void fsm_assign(FsmTable T, int64_t min_support, unsigned long long* 
     } else {
       T.id[h] = -1;
     }
+  }
+}
+
+// Row offsets of one domain pass: the slots of IDs [id_lo, id_lo + id_n)
+// get the first word of each orbit's row (rowoff, relative to the pass's
+// bitmap buffer); the others are marked out of the pass.
+__global__ void fsm_pass_rows(FsmTable T, const int64_t* rowoff, int32_t id_lo, int32_t id_n) {
+  for (int64_t h = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; h <= (int64_t)T.mask;
+       h += (int64_t)gridDim.x * blockDim.x) {
+    if (!T.keys[h]) continue;
+    const int32_t id = T.id[h], j = id - id_lo;
+    if (id >= 0 && j < id_n) {
+      const int64_t* r = rowoff + (int64_t)j * 4;
+      T.off[h] = make_int4((int32_t)r[0], (int32_t)r[1], (int32_t)r[2], (int32_t)r[3]);
+    } else {
+      T.off[h] = make_int4(-1, 0, 0, 0);
+    }
+  }
+}
+
+// Filter flags of a level once its supports are known (freq by compact ID)
+__global__ void fsm_set_frequent(FsmTable T, const uint8_t* freq) {
+  for (int64_t h = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; h <= (int64_t)T.mask;
+       h += (int64_t)gridDim.x * blockDim.x) {
+    if (T.keys[h] && T.id[h] >= 0) T.frequent[h] = freq[T.id[h]];
   }
 }
 
@@ -433,13 +472,12 @@ __global__ void __launch_bounds__(256) fsm_popcount(const uint32_t* dom, const i
 }
 
 // level-1 Filter flags per arc: the arc's 1-edge pattern is frequent
-__global__ void fsm_arc_flags(FsmArgs A, const uint8_t* freq1, uint8_t* out) {
+__global__ void fsm_arc_flags(FsmArgs A, uint8_t* out) {
   for (int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; a < A.narcs;
        a += (int64_t)gridDim.x * blockDim.x) {
     int32_t v[4];
     int orb[4];
-    const int id = fsm_find(A.T, fsm_edge(A.lab, A.src[a], A.col[a], v, orb));
-    out[a] = (id >= 0 && freq1[id]) ? 1 : 0;
+    out[a] = fsm_frequent(A.T, fsm_edge(A.lab, A.src[a], A.col[a], v, orb)) ? 1 : 0;
   }
 }
 
@@ -528,14 +566,17 @@ int64_t orbit_words(unsigned long long key, int o, const std::vector<int64_t>& p
 struct FsmBuffers {
   DevArr<unsigned long long> keys[3], slot_cnt, kbi, cbi, ctr, pop;
   DevArr<int32_t> ids[3];
-  DevArr<uint8_t> freq_arc, freq[3];
+  DevArr<uint8_t> frequent[3], freq_arc, freq;
+  DevArr<int4> off;
   DevArr<int64_t> rowoff;
   ~FsmBuffers() {
     for (int i = 0; i < 3; i++) {
       keys[i].release();
       ids[i].release();
-      freq[i].release();
+      frequent[i].release();
     }
+    off.release();
+    freq.release();
     slot_cnt.release();
     kbi.release();
     cbi.release();
@@ -568,8 +609,11 @@ pgm_status fsm_run(Graph& g, int max_edges, int64_t min_support, std::vector<pgm
   Profiler& prof = profiler();
   *examined = 0;
   for (int l = 1; l <= max_edges; l++) {
+    PGM_NVTX(kNvtxLevel[l]);
     PGM_TRY(B.keys[l - 1].reserve(slots));
     PGM_TRY(B.ids[l - 1].reserve(slots));
+    PGM_TRY(B.frequent[l - 1].reserve(slots));
+    PGM_TRY(B.off.reserve(slots));  // only the current level has domain passes
     PGM_TRY_CUDA(cudaMemsetAsync(B.keys[l - 1].p, 0, slots * sizeof(unsigned long long), s));
     PGM_TRY_CUDA(cudaMemsetAsync(B.slot_cnt.p, 0, slots * sizeof(unsigned long long), s));
     PGM_TRY_CUDA(cudaMemsetAsync(B.ctr.p, 0, kCtrSlots * sizeof(unsigned long long), s));
@@ -582,11 +626,8 @@ pgm_status fsm_run(Graph& g, int max_edges, int64_t min_support, std::vector<pgm
     A.lab = g.labels;
     A.rank = g.label_rank;
     A.narcs = g.narcs;
-    A.T = FsmTable{B.keys[l - 1].p, B.ids[l - 1].p, B.slot_cnt.p, slots - 1};
-    if (l == 3) {
-      A.T2 = FsmTable{B.keys[1].p, B.ids[1].p, nullptr, slots - 1};
-      A.freq2 = B.freq[1].p;
-    }
+    A.T = FsmTable{B.keys[l - 1].p, B.ids[l - 1].p, B.frequent[l - 1].p, B.off.p, B.slot_cnt.p, slots - 1};
+    if (l == 3) A.T2 = FsmTable{B.keys[1].p, B.ids[1].p, B.frequent[1].p, nullptr, nullptr, slots - 1};
     A.freq_arc = B.freq_arc.p;
     A.queue = B.ctr.p + kCtrQueue;
     A.err = B.ctr.p + kCtrErr;
@@ -633,7 +674,8 @@ pgm_status fsm_run(Graph& g, int max_edges, int64_t min_support, std::vector<pgm
       size_t free_b = 0, total_b = 0;
       PGM_TRY_CUDA(cudaMemGetInfo(&free_b, &total_b));
       const double budget = std::min((double)kFsmDomainBytes, 0.6 * (double)free_b + (double)dom.cap * 4.0);
-      const int64_t budget_words = std::max<int64_t>((int64_t)(budget / 4.0), 1);
+      // row offsets are int32 words in the slots: at most 2^31 - 1 words per pass
+      const int64_t budget_words = std::max<int64_t>(std::min<int64_t>((int64_t)(budget / 4.0), INT32_MAX), 1);
       std::vector<int64_t> off;
       for (int64_t lo = 0; lo < nid;) {
         int64_t hi = lo, tot = 0;
@@ -652,10 +694,9 @@ pgm_status fsm_run(Graph& g, int max_edges, int64_t min_support, std::vector<pgm
         PGM_TRY(B.pop.reserve((size_t)(cn * 4)));
         PGM_TRY_CUDA(cudaMemcpyAsync(B.rowoff.p, off.data(), off.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s));
         PGM_TRY_CUDA(cudaMemsetAsync(dom.p, 0, (size_t)tot * sizeof(uint32_t), s));
+        fsm_pass_rows<<<num_sms() * 4, 256, 0, s>>>(A.T, B.rowoff.p, (int32_t)lo, (int32_t)cn);
+        PGM_CHECK_LAUNCH();
         A.dom = dom.p;
-        A.rowoff = B.rowoff.p;
-        A.id_lo = (int32_t)lo;
-        A.id_n = (int32_t)cn;
         PGM_TRY(launch(1));
         fsm_popcount<<<(int)std::min<int64_t>(cn * 4, (int64_t)num_sms() * 16), 256, 0, s>>>(dom.p, B.rowoff.p,
                                                                                              cn * 4, B.pop.p);
@@ -694,10 +735,12 @@ pgm_status fsm_run(Graph& g, int max_edges, int64_t min_support, std::vector<pgm
     }
     if (nfreq == 0) break;  // nothing to extend
     if (l < max_edges) {
-      PGM_TRY(B.freq[l - 1].reserve(fr.size()));
-      PGM_TRY_CUDA(cudaMemcpyAsync(B.freq[l - 1].p, fr.data(), fr.size(), cudaMemcpyHostToDevice, s));
+      PGM_TRY(B.freq.reserve(fr.size()));
+      PGM_TRY_CUDA(cudaMemcpyAsync(B.freq.p, fr.data(), fr.size(), cudaMemcpyHostToDevice, s));
+      fsm_set_frequent<<<num_sms() * 4, 256, 0, s>>>(A.T, B.freq.p);
+      PGM_CHECK_LAUNCH();
       if (l == 1) {
-        fsm_arc_flags<<<g1, threads, 0, s>>>(A, B.freq[0].p, B.freq_arc.p);
+        fsm_arc_flags<<<g1, threads, 0, s>>>(A, B.freq_arc.p);
         PGM_CHECK_LAUNCH();
       }
       PGM_TRY_CUDA(cudaStreamSynchronize(s));  // fr is a host buffer of this iteration
@@ -741,6 +784,7 @@ static pgm_status graph_set_labels(Graph& g, const int32_t* labels) {
 extern "C" {
 
 pgm_status pgm_graph_set_labels(pgm_graph* g, const int32_t* labels) {
+  PGM_NVTX("pgm_graph_set_labels");
   if (!g || (!labels && g->g.n > 0)) {
     pgm::set_error("pgm_graph_set_labels: null argument");
     return PGM_EINVAL;
@@ -750,6 +794,7 @@ pgm_status pgm_graph_set_labels(pgm_graph* g, const int32_t* labels) {
 
 pgm_status pgm_fsm(pgm_graph* g, int32_t max_edges, int64_t min_support, pgm_fsm_pattern* out, int32_t cap,
                    int32_t* n_out) {
+  PGM_NVTX("pgm_fsm");
   if (!g || !n_out || cap < 0 || (cap > 0 && !out)) {
     pgm::set_error("pgm_fsm: bad arguments");
     return PGM_EINVAL;

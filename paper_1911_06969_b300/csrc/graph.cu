@@ -488,6 +488,7 @@ extern "C" {
 
 pgm_status pgm_graph_create_csr(int32_t n, const int64_t* rowptr, const int32_t* col, uint32_t flags,
                                 void* stream, pgm_graph** out) {
+  PGM_NVTX("pgm_graph_create_csr");
   if (!out) {
     pgm::set_error("pgm_graph_create_csr: null out");
     return PGM_EINVAL;
@@ -507,6 +508,7 @@ pgm_status pgm_graph_create_csr(int32_t n, const int64_t* rowptr, const int32_t*
 
 pgm_status pgm_graph_create_csr_dev(int32_t n, const int64_t* rowptr_dev, const int32_t* col_dev,
                                     int64_t narcs, uint32_t flags, void* stream, pgm_graph** out) {
+  PGM_NVTX("pgm_graph_create_csr_dev");
   if (!out || (narcs > 0 && !col_dev)) {
     pgm::set_error("pgm_graph_create_csr_dev: bad arguments");
     return PGM_EINVAL;
@@ -526,6 +528,7 @@ pgm_status pgm_graph_create_csr_dev(int32_t n, const int64_t* rowptr_dev, const 
 }
 
 pgm_status pgm_graph_orient_by_degree(pgm_graph* g) {
+  PGM_NVTX("pgm_graph_orient_by_degree");
   if (!g) {
     pgm::set_error("pgm_graph_orient_by_degree: null graph");
     return PGM_EINVAL;

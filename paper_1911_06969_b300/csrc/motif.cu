@@ -1067,6 +1067,7 @@ struct MotifRun {
   pgm_status run3(int32_t v_lo, int32_t v_hi) { return launch_l2<mSum>(args(v_lo, v_hi), "extend_sum"); }
 
   pgm_status run4(int32_t v_lo, int32_t v_hi) {
+    PGM_NVTX("motif4 levels 2-4");
     const int64_t a_lo = g.h_rp[v_lo], a_hi = g.h_rp[v_hi];
     const int64_t E = a_hi - a_lo;  // arcs; arcs to lower neighbours get zero children
     if (E == 0) return PGM_OK;
@@ -1220,6 +1221,7 @@ pgm_status count_motifs_on(Graph& g, Workspace& ws, cudaStream_t s, int k, int32
 extern "C" {
 
 pgm_status pgm_count_motifs(pgm_graph* g, int32_t k, uint64_t* out_counts, int32_t cap) {
+  PGM_NVTX("pgm_count_motifs");
   if (!g || !out_counts) {
     pgm::set_error("pgm_count_motifs: null argument");
     return PGM_EINVAL;
@@ -1238,6 +1240,7 @@ pgm_status pgm_count_motifs(pgm_graph* g, int32_t k, uint64_t* out_counts, int32
 
 pgm_status pgm_count_motifs_range(pgm_graph* g, int32_t k, int32_t v_lo, int32_t v_hi,
                                   uint64_t* out_counts, int32_t cap) {
+  PGM_NVTX("pgm_count_motifs_range");
   if (!g || !out_counts) {
     pgm::set_error("pgm_count_motifs_range: null argument");
     return PGM_EINVAL;

@@ -396,6 +396,7 @@ struct MgRun {
 
   // entries [0, E) of level i (tuples `tup`, or arcs [e_lo, e_lo + E) for i = 2)
   pgm_status level(int i, const int32_t* tup, int64_t E, int64_t e_lo) {
+    PGM_NVTX(kNvtxLevel[i < 13 ? i : 12]);
     if (E <= 0) return PGM_OK;
     lvl_size[i] += (double)E;
     MgArgs A;
@@ -613,10 +614,12 @@ static pgm_status list_motifs_to(pgm_graph* g, int32_t k, int32_t* out, int64_t 
 }
 
 pgm_status pgm_list_motifs(pgm_graph* g, int32_t k, int32_t* out_dev, int64_t cap_rows, int64_t* n_rows) {
+  PGM_NVTX("pgm_list_motifs");
   return list_motifs_to(g, k, out_dev, cap_rows, n_rows, false, "pgm_list_motifs");
 }
 
 pgm_status pgm_list_motifs_host(pgm_graph* g, int32_t k, int32_t* out_host, int64_t cap_rows, int64_t* n_rows) {
+  PGM_NVTX("pgm_list_motifs_host");
   return list_motifs_to(g, k, out_host, cap_rows, n_rows, true, "pgm_list_motifs_host");
 }
 

@@ -177,6 +177,7 @@ pgm_status pgm_server_create(int64_t budget_bytes, int32_t max_inflight, pgm_ser
 
 pgm_status pgm_server_add_graph(pgm_server* s, int32_t n, const int64_t* rowptr, const int32_t* col,
                                 int32_t* graph_id) {
+  PGM_NVTX("pgm_server_add_graph");
   if (!s || !graph_id) {
     pgm::set_error("pgm_server_add_graph: null argument");
     return PGM_EINVAL;
