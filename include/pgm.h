@@ -66,8 +66,9 @@ typedef struct {
 } pgm_graph_stats;
 
 /* Tunables (pgm_set_options / pgm_get_options).  A zero field keeps the
- * current value, except `profile`, `clique_engine` and `motif_order`, which
- * every call sets (0 = off / auto). */
+ * current value, except `profile`, `clique_engine`, `motif_order`,
+ * `count_headroom_log2` and `fsm_domain_order`, which every call sets
+ * (0 = off / auto). */
 typedef struct {
   int32_t block_threads;   /* threads per block of the warp-per-parent kernels, 64..512 (default 256) */
   int32_t warp_stage_cap;  /* per-warp shared-memory staging capacity, ints (default 512)     */
@@ -96,6 +97,10 @@ typedef struct {
                                     children adjacent to v0 finds their common neighbours with v1 by
                                     extending the members of N(v1) (one scan per edge), fewer scan each
                                     child's own list (default 32; 1 = always, 2^30 = never)          */
+  int32_t fsm_domain_order;      /* pgm_fsm, domain passes of 2-edge patterns (every call sets this field):
+                                    0 = auto (by centre vertex in label order when at least half the
+                                    arcs are frequent and the pass's bitmaps exceed half of L2, else by
+                                    first edge), 1 = by first edge, 2 = by centre; results are the same */
 } pgm_options;
 
 /* Per-call profile (when options.profile = 1): one record per kernel phase. */

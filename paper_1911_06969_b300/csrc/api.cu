@@ -29,7 +29,7 @@ const char* get_error() { return t_err.c_str(); }
 static std::atomic<uint64_t> g_launches{0};
 void note_launches(uint64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
-static pgm_options g_opts = {256, 512, 0, 0, (int64_t)1 << 31, 0, 2, 0, 4, 1024, 0, 0, 32};
+static pgm_options g_opts = {256, 512, 0, 0, (int64_t)1 << 31, 0, 2, 0, 4, 1024, 0, 0, 32, 0};
 
 pgm_options& options() { return g_opts; }
 
@@ -369,6 +369,11 @@ pgm_status pgm_set_options(const pgm_options* o) {
     }
     next.motif_b_side_min = v.motif_b_side_min;
   }
+  if (v.fsm_domain_order < 0 || v.fsm_domain_order > 2) {
+    pgm::set_error("fsm_domain_order must be 0 (auto), 1 (by first edge) or 2 (by centre)");
+    return PGM_EINVAL;
+  }
+  next.fsm_domain_order = v.fsm_domain_order;
   next.profile = v.profile ? 1 : 0;
   pgm::options() = next;
   return PGM_OK;

@@ -162,6 +162,9 @@ struct Graph {
   int32_t* labels = nullptr;   // frequent subgraph mining: vertex labels (pgm_graph_set_labels)
   int32_t* label_rank = nullptr;       // vertex -> its index among the vertices of its label
   std::vector<int64_t> h_label_count;  // vertices per label
+  int32_t* wedge_centres = nullptr;    // vertices of degree >= 2 in (label, ID) order
+  int64_t* wedge_prefix = nullptr;     // exclusive prefix of C(d, 2) over wedge_centres (n_centres + 1)
+  int64_t n_wedge_centres = 0, n_wedges = 0;
   int32_t* hub_idx = nullptr;  // motifs: vertex -> row of hub_bits, or -1
   uint32_t* hub_bits = nullptr;  // motifs: adjacency bitmaps of the highest-degree vertices
   int64_t hub_words = 0;       // 32-bit words per bitmap row

@@ -111,6 +111,9 @@ struct FsmArgs {
   const int32_t* rev;  // arc -> reverse arc
   const int32_t* lab;  // vertex labels
   const int32_t* rank; // vertex -> index among the vertices of its label (bit of a domain row)
+  const int32_t* centres;   // level 2: vertices of degree >= 2 in (label, ID) order
+  const int64_t* wprefix;   // level 2: exclusive prefix of C(d, 2) over centres
+  int64_t ncentres, nwedges;
   int64_t narcs;
   int mode;            // 0: insert and count pattern keys, 1: mark domains
   FsmTable T;          // this level's patterns
@@ -128,7 +131,7 @@ struct FsmArgs {
 // with rows in this pass; the bit positions (label ranks) are loaded before
 // the probe, so that they do not wait behind it.
 __device__ __forceinline__ void fsm_emit(const FsmArgs& A, bool valid, unsigned long long key, int nv,
-                                         const int32_t (&v)[4], const int (&orb)[4]) {
+                                         const int32_t (&v)[4], const int (&orb)[4], bool centre_first) {
   if (A.mode == 0) {
     const int h = valid ? fsm_insert(A.T, key) : -1;
     if (valid && h < 0) atomicAdd(A.err, 1ull);
@@ -149,7 +152,14 @@ __device__ __forceinline__ void fsm_emit(const FsmArgs& A, bool valid, unsigned 
       if (i < nv) {
         const int o = orb[i];
         const int32_t row = o == 0 ? e1.x : (o == 1 ? e1.y : (o == 2 ? e1.z : e1.w));
-        atomicOr(A.dom + row + (r[i] >> 5), 1u << (r[i] & 31));
+        uint32_t* word = A.dom + row + (r[i] >> 5);
+        const uint32_t bit = 1u << (r[i] & 31);
+        // v[0] is a centre shared by the warp's lanes and by the warps on the
+        // same hub: after its first set, a cached read (stale only towards 0)
+        // spares the same-word atomics (checking the other shared vertex as
+        // well, or every vertex, measured slower)
+        if (i == 0 && centre_first && (*word & bit)) continue;
+        atomicOr(word, bit);
       }
   }
 }
@@ -260,7 +270,7 @@ __global__ void __launch_bounds__(256) fsm_level1(FsmArgs A) {
       valid = u < w;
       if (valid) key = fsm_edge(A.lab, u, w, v, orb);
     }
-    fsm_emit(A, valid, key, 2, v, orb);
+    fsm_emit(A, valid, key, 2, v, orb, false);
   }
 }
 
@@ -295,8 +305,79 @@ __device__ __forceinline__ FsmPair fsm_pair(const FsmArgs& A, int64_t ea, int32_
   return r;
 }
 
-// one warp per frequent 1-edge embedding, grabbed from a queue over arcs
-__global__ void __launch_bounds__(256) fsm_level2(FsmArgs A) {
+// Level 2 by centre.  A 2-edge embedding is a pair of frequent edges at a
+// common vertex, its centre; taking each pair {i < j} of a centre's list
+// once gives each embedding once.  The pairs of all centres form one index
+// space (wprefix), cut into chunks of 32 * kFsmPairIters pairs that warps
+// take from a queue, so hubs spread over many warps.  Centres come in
+// (label, ID) order: at any time the warps touch the patterns -- and the
+// domain rows -- of one centre label, few enough to stay in L2, and the
+// centres' own bits are set in rank order.
+constexpr int kFsmPairIters = 8;
+
+__global__ void __launch_bounds__(256, 4) fsm_level2_centres(FsmArgs A) {
+  const int lane = threadIdx.x & 31;
+  unsigned long long seen = 0;
+  for (;;) {
+    unsigned long long p0 = 0;
+    if (lane == 0) p0 = atomicAdd(A.queue, 32ull * kFsmPairIters);
+    p0 = __shfl_sync(kFull, p0, 0);
+    if ((int64_t)p0 >= A.nwedges) break;
+    // centre of the chunk's first pair: the largest q with wprefix[q] <= p0
+    int64_t q = 0;
+    if (lane == 0) {
+      int64_t lo = 0, hi = A.ncentres - 1;
+      while (lo < hi) {
+        const int64_t mid = (lo + hi + 1) >> 1;
+        if (A.wprefix[mid] <= (int64_t)p0) lo = mid; else hi = mid - 1;
+      }
+      q = lo;
+    }
+    q = __shfl_sync(kFull, q, 0);
+    for (int it = 0; it < kFsmPairIters; it++) {
+      const int64_t t = (int64_t)p0 + it * 32 + lane;
+      bool ok = false;
+      int32_t v[4] = {0, 0, 0, 0};
+      int orb[4] = {0, 0, 0, 0};
+      unsigned long long key = 0;
+      if (t < A.nwedges) {
+        while (A.wprefix[q + 1] <= t) q++;  // later centres of the chunk (every centre has a pair)
+        const int32_t c = A.centres[q];
+        const int64_t r0 = A.rp[c];
+        const int64_t d = A.rp[c + 1] - r0;
+        const int64_t tl = t - A.wprefix[q];
+        // pair tl in the order (0,1), (0,2), ..., (1,2), ...: row i starts at
+        // i (2d - i - 1) / 2; a root estimate (single precision below 2^20
+        // neighbours, double above, where float would be thousands of rows
+        // off), then exact correction
+        int64_t i;
+        if (d < (1 << 20)) {
+          const float b = (float)(2 * d - 1);
+          i = (int64_t)((b - sqrtf(fmaxf(b * b - 8.0f * (float)tl, 0.0f))) * 0.5f);
+        } else {
+          const double b = (double)(2 * d - 1);
+          i = (int64_t)((b - sqrt(fmax(b * b - 8.0 * (double)tl, 0.0))) * 0.5);
+        }
+        i = max((int64_t)0, min(i, d - 2));
+        while (i > 0 && i * (2 * d - i - 1) / 2 > tl) i--;
+        while (i + 1 <= d - 2 && (i + 1) * (2 * d - i - 2) / 2 <= tl) i++;
+        const int64_t j = i + 1 + (tl - i * (2 * d - i - 1) / 2);
+        seen++;
+        ok = A.freq_arc[r0 + i] && A.freq_arc[r0 + j];
+        if (ok) key = fsm_wedge(A.lab, c, A.col[r0 + i], A.col[r0 + j], v, orb);
+      }
+      fsm_emit(A, ok, key, 3, v, orb, true);  // v[0] = the centre
+    }
+  }
+  seen = warp_sum(seen);
+  if (lane == 0 && seen) atomicAdd(A.stat, seen);
+}
+
+// Level 2 by first edge: one warp per frequent 1-edge embedding e_a (a
+// queue over arcs), lanes over N(u) then N(w) for the second edge e_b > e_a.
+// Cost ~ the frequent arcs' d(u) + d(w): the cheaper order when the Filter
+// has dropped many edges.
+__global__ void __launch_bounds__(256) fsm_level2_arcs(FsmArgs A) {
   const int lane = threadIdx.x & 31;
   unsigned long long seen = 0;
   for (;;) {
@@ -313,7 +394,7 @@ __global__ void __launch_bounds__(256) fsm_level2(FsmArgs A) {
         int32_t v[4] = {0, 0, 0, 0};
         int orb[4] = {0, 0, 0, 0};
         const unsigned long long key = pr.ok ? fsm_wedge(A.lab, pr.centre, pr.x, pr.y, v, orb) : 0ull;
-        fsm_emit(A, pr.ok, key, 3, v, orb);
+        fsm_emit(A, pr.ok, key, 3, v, orb, false);
       }
       if (lane == 0) seen += (unsigned long long)(du + dw);
     }
@@ -331,7 +412,7 @@ __global__ void __launch_bounds__(256) fsm_level2(FsmArgs A) {
 //   list of y (end of e_b): 3-path x - c - y - q,          needs e_c > e_a
 // (e_c sharing a vertex with e_a must exceed e_b; the closing edge (x, y) of
 // a triangle is taken from x's list only).
-__global__ void __launch_bounds__(256) fsm_level3(FsmArgs A) {
+__global__ void __launch_bounds__(256, 6) fsm_level3(FsmArgs A) {
   const int lane = threadIdx.x & 31;
   unsigned long long seen = 0;
   for (;;) {
@@ -391,7 +472,7 @@ __global__ void __launch_bounds__(256) fsm_level3(FsmArgs A) {
                 }
               }
             }
-            fsm_emit(A, ok, key, nv, v, orb);  // a triangle has 3 vertices, the others 4
+            fsm_emit(A, ok, key, nv, v, orb, false);  // a triangle has 3 vertices, the others 4
           }
         }
       }
@@ -604,7 +685,18 @@ pgm_status fsm_run(Graph& g, int max_edges, int64_t min_support, std::vector<pgm
   PGM_TRY(B.freq_arc.reserve((size_t)std::max<int64_t>(g.narcs, 1)));
   const int threads = 256;
   const int g1 = std::max(1, std::min(num_sms() * 8, (int)((g.narcs + threads - 1) / threads)));
-  const int gq2 = grid_for((const void*)fsm_level2, threads, 0);
+  const int gq2c = grid_for((const void*)fsm_level2_centres, threads, 0);
+  const int gq2a = grid_for((const void*)fsm_level2_arcs, threads, 0);
+  // Level 2 by centre enumerates every pair of edges at a vertex (about
+  // sum d^2 / 2 candidates), by first edge the lists of the frequent arcs
+  // (about f sum d^2 for a fraction f of frequent arcs).  The key pass goes
+  // by first edge (hub centres would make many warps count into the same
+  // slots); a domain pass goes by centre when at least half the arcs are
+  // frequent and its bitmaps exceed half of L2 (below that they stay cached
+  // in either order).
+  bool centre_ok = false, by_centre = false;
+  int l2_bytes = 0;
+  PGM_TRY_CUDA(cudaDeviceGetAttribute(&l2_bytes, cudaDevAttrL2CacheSize, device_id()));
   const int gq3 = grid_for((const void*)fsm_level3, threads, 0);
   Profiler& prof = profiler();
   *examined = 0;
@@ -625,6 +717,10 @@ pgm_status fsm_run(Graph& g, int max_edges, int64_t min_support, std::vector<pgm
     A.rev = g.rev;
     A.lab = g.labels;
     A.rank = g.label_rank;
+    A.centres = g.wedge_centres;
+    A.wprefix = g.wedge_prefix;
+    A.ncentres = g.n_wedge_centres;
+    A.nwedges = g.n_wedges;
     A.narcs = g.narcs;
     A.T = FsmTable{B.keys[l - 1].p, B.ids[l - 1].p, B.frequent[l - 1].p, B.off.p, B.slot_cnt.p, slots - 1};
     if (l == 3) A.T2 = FsmTable{B.keys[1].p, B.ids[1].p, B.frequent[1].p, nullptr, nullptr, slots - 1};
@@ -641,7 +737,10 @@ pgm_status fsm_run(Graph& g, int max_edges, int64_t min_support, std::vector<pgm
       if (l == 1 || g.narcs == 0)
         fsm_level1<<<g1, threads, 0, s>>>(A);
       else if (l == 2)
-        fsm_level2<<<gq2, threads, 0, s>>>(A);
+        if (mode == 1 && by_centre)
+          fsm_level2_centres<<<gq2c, threads, 0, s>>>(A);
+        else
+          fsm_level2_arcs<<<gq2a, threads, 0, s>>>(A);
       else
         fsm_level3<<<gq3, threads, 0, s>>>(A);
       PGM_CHECK_LAUNCH();
@@ -694,6 +793,9 @@ pgm_status fsm_run(Graph& g, int max_edges, int64_t min_support, std::vector<pgm
         PGM_TRY(B.pop.reserve((size_t)(cn * 4)));
         PGM_TRY_CUDA(cudaMemcpyAsync(B.rowoff.p, off.data(), off.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s));
         PGM_TRY_CUDA(cudaMemsetAsync(dom.p, 0, (size_t)tot * sizeof(uint32_t), s));
+        const int order = options().fsm_domain_order;
+        by_centre = g.n_wedges > 0 &&
+                    (order == 2 || (order == 0 && centre_ok && 4.0 * (double)tot > 0.5 * (double)l2_bytes));
         fsm_pass_rows<<<num_sms() * 4, 256, 0, s>>>(A.T, B.rowoff.p, (int32_t)lo, (int32_t)cn);
         PGM_CHECK_LAUNCH();
         A.dom = dom.p;
@@ -734,6 +836,12 @@ pgm_status fsm_run(Graph& g, int max_edges, int64_t min_support, std::vector<pgm
       res.push_back(p);
     }
     if (nfreq == 0) break;  // nothing to extend
+    if (l == 1) {
+      unsigned long long freq_edges = 0;
+      for (int64_t i = 0; i < nid; i++)
+        if (fr[(size_t)i]) freq_edges += cnt[(size_t)i];
+      centre_ok = 4.0 * (double)freq_edges >= (double)g.narcs && g.n_wedges > 0;  // 2 arcs per edge
+    }
     if (l < max_edges) {
       PGM_TRY(B.freq.reserve(fr.size()));
       PGM_TRY_CUDA(cudaMemcpyAsync(B.freq.p, fr.data(), fr.size(), cudaMemcpyHostToDevice, s));
@@ -766,6 +874,33 @@ static pgm_status graph_set_labels(Graph& g, const int32_t* labels) {
     rank[(size_t)v] = (int32_t)count[(size_t)labels[v]]++;
   }
   std::lock_guard<std::recursive_mutex> lk(g.mu);
+  // wedge centres (degree >= 2) in (label, ID) order and the prefix of their pair counts
+  PGM_TRY(graph_host_rp(g));
+  std::vector<int64_t> start(count.size() + 1, 0);
+  for (size_t l = 0; l < count.size(); l++) start[l + 1] = start[l] + count[l];
+  std::vector<int32_t> order((size_t)g.n);
+  for (int32_t v = 0; v < g.n; v++) order[(size_t)(start[(size_t)labels[v]] + rank[(size_t)v])] = v;
+  std::vector<int32_t> centres;
+  std::vector<int64_t> wprefix(1, 0);
+  for (int32_t v : order) {
+    const int64_t d = g.h_rp[(size_t)v + 1] - g.h_rp[(size_t)v];
+    if (d < 2) continue;
+    centres.push_back(v);
+    wprefix.push_back(wprefix.back() + d * (d - 1) / 2);
+  }
+  if (g.wedge_centres) cudaFree(g.wedge_centres);
+  if (g.wedge_prefix) cudaFree(g.wedge_prefix);
+  g.wedge_centres = nullptr;
+  g.wedge_prefix = nullptr;
+  PGM_TRY_CUDA(cudaMalloc(&g.wedge_centres, std::max<size_t>(centres.size(), 1) * sizeof(int32_t)));
+  PGM_TRY_CUDA(cudaMalloc(&g.wedge_prefix, wprefix.size() * sizeof(int64_t)));
+  if (!centres.empty())
+    PGM_TRY_CUDA(cudaMemcpyAsync(g.wedge_centres, centres.data(), centres.size() * sizeof(int32_t),
+                                 cudaMemcpyHostToDevice, g.stream));
+  PGM_TRY_CUDA(cudaMemcpyAsync(g.wedge_prefix, wprefix.data(), wprefix.size() * sizeof(int64_t),
+                               cudaMemcpyHostToDevice, g.stream));
+  g.n_wedge_centres = (int64_t)centres.size();
+  g.n_wedges = wprefix.back();
   const size_t bytes = (size_t)std::max<int32_t>(g.n, 1) * sizeof(int32_t);
   if (!g.labels) PGM_TRY_CUDA(cudaMalloc(&g.labels, bytes));
   if (!g.label_rank) PGM_TRY_CUDA(cudaMalloc(&g.label_rank, bytes));

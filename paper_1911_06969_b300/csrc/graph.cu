@@ -226,11 +226,16 @@ void graph_free(Graph& g) {
   if (g.hub_idx) cudaFree(g.hub_idx);
   if (g.labels) cudaFree(g.labels);
   if (g.label_rank) cudaFree(g.label_rank);
+  if (g.wedge_centres) cudaFree(g.wedge_centres);
+  if (g.wedge_prefix) cudaFree(g.wedge_prefix);
   if (g.hub_bits) cudaFree(g.hub_bits);
   g.rp = g.col = g.dag_rp = g.dag_col = g.gid = g.up = g.src = g.hub_idx = g.rev = nullptr;
   g.hub_bits = nullptr;
   g.labels = nullptr;
   g.label_rank = nullptr;
+  g.wedge_centres = nullptr;
+  g.wedge_prefix = nullptr;
+  g.n_wedge_centres = g.n_wedges = 0;
   g.h_label_count.clear();
   g.nhubs = 0;
   g.ws.release_all();

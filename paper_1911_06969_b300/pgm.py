@@ -58,7 +58,8 @@ class pgm_options(C.Structure):
                 ("blocks_per_sm", C.c_int32), ("level_budget", C.c_int64), ("profile", C.c_int32),
                 ("reverse_ratio", C.c_int32), ("clique_engine", C.c_int32),
                 ("bitset_forward_ratio", C.c_int32), ("bitset_smem_degree", C.c_int32),
-                ("motif_order", C.c_int32), ("count_headroom_log2", C.c_int32), ("motif_b_side_min", C.c_int32)]
+                ("motif_order", C.c_int32), ("count_headroom_log2", C.c_int32), ("motif_b_side_min", C.c_int32),
+                ("fsm_domain_order", C.c_int32)]
 
 
 class pgm_phase(C.Structure):

@@ -80,6 +80,22 @@ def test_random_small(max_edges):
         check(g, lab, max_edges, (1, 2, 4))
 
 
+@pytest.mark.parametrize("order", [1, 2])
+def test_domain_orders(order):
+    """Both enumerations of the 2-edge domain passes (by first edge, by
+    centre vertex in label order; the automatic choice takes the centre
+    order only for bitmaps larger than half of L2) give the oracle's lists,
+    with and without the Filter dropping edges."""
+    try:
+        pgm.pgm_set_options(fsm_domain_order=order)
+        for i, g in enumerate([gg.complete(9), gg.star(40), gg.barabasi_albert(800, 3, seed=7),
+                               gg.erdos_renyi(600, 0.02, seed=8), gg.empty(4)]):
+            lab = gg.vertex_labels(g.n, 3, seed=20 + i, skew=0.9)
+            check(g, lab, 3, (1, 3, 40))
+    finally:
+        pgm.pgm_set_options(fsm_domain_order=0)
+
+
 # ----------------------------------------------------------- medium graphs
 @pytest.mark.parametrize("sigma", [1, 20, 100, 10**6])
 def test_er_medium(sigma):
