@@ -214,6 +214,86 @@ pgm_status read_counters(const unsigned long long* dev, unsigned long long* host
   return PGM_OK;
 }
 
+// ----------------------------------------------------------- device memory
+namespace {
+struct DevPool {
+  cudaMemPool_t pool = nullptr;
+  cudaStream_t s = nullptr;  // stream of the pool's allocations and frees
+};
+constexpr int kMaxDevices = 64;
+std::mutex g_pool_mu;
+DevPool g_pools[kMaxDevices];
+
+DevPool* pool_here(cudaError_t& e) {
+  int dev = 0;
+  e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return nullptr;
+  if (dev < 0 || dev >= kMaxDevices) {
+    e = cudaErrorInvalidDevice;
+    return nullptr;
+  }
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  DevPool& P = g_pools[dev];
+  if (!P.pool) {
+    cudaMemPoolProps props;
+    memset(&props, 0, sizeof(props));
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    e = cudaMemPoolCreate(&P.pool, &props);
+    if (e != cudaSuccess) {
+      P.pool = nullptr;
+      return nullptr;
+    }
+    uint64_t keep = kPoolKeepBytes;
+    e = cudaMemPoolSetAttribute(P.pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&P.s, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+      cudaMemPoolDestroy(P.pool);
+      P.pool = nullptr;
+      P.s = nullptr;
+      return nullptr;
+    }
+  }
+  e = cudaSuccess;
+  return &P;
+}
+}  // namespace
+
+cudaError_t dev_malloc(void** p, size_t bytes) {
+  *p = nullptr;
+  cudaError_t e;
+  DevPool* P = pool_here(e);
+  if (!P) return e;
+  e = cudaMallocFromPoolAsync(p, bytes, P->pool, P->s);
+  if (e == cudaErrorMemoryAllocation) {  // give the cached blocks back and try once more
+    cudaGetLastError();
+    cudaStreamSynchronize(P->s);
+    cudaMemPoolTrimTo(P->pool, 0);
+    e = cudaMallocFromPoolAsync(p, bytes, P->pool, P->s);
+  }
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    return e;
+  }
+  e = cudaStreamSynchronize(P->s);  // complete: usable from every stream
+  if (e != cudaSuccess) {
+    cudaFreeAsync(*p, P->s);
+    *p = nullptr;
+  }
+  return e;
+}
+
+cudaError_t dev_free(void* p) {
+  if (!p) return cudaSuccess;
+  cudaError_t e;
+  DevPool* P = pool_here(e);
+  if (!P) return e;
+  e = cudaDeviceSynchronize();  // every user of the block has finished, as with cudaFree
+  const cudaError_t f = cudaFreeAsync(p, P->s);
+  return e != cudaSuccess ? e : f;
+}
+
 void Workspace::release_all() {
   for (int i = 0; i < kMaxLevels; i++) {
     cnt[i].release();

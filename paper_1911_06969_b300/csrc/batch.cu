@@ -436,12 +436,12 @@ pgm_status pgm_batch_create(int32_t G, const int64_t* vtx_off, const int64_t* ro
   // vertex -> graph map and the no-crossing-arc check
   int64_t* d_off = nullptr;
   unsigned* d_bad = nullptr;
-  if (cudaMalloc(&b->g.gid, (size_t)std::max<int64_t>(n, 1) * sizeof(int32_t)) != cudaSuccess ||
-      cudaMalloc(&d_off, ((size_t)G + 1) * sizeof(int64_t)) != cudaSuccess ||
-      cudaMalloc(&d_bad, sizeof(unsigned)) != cudaSuccess) {
+  if (pgm::dev_malloc(&b->g.gid, (size_t)std::max<int64_t>(n, 1) * sizeof(int32_t)) != cudaSuccess ||
+      pgm::dev_malloc(&d_off, ((size_t)G + 1) * sizeof(int64_t)) != cudaSuccess ||
+      pgm::dev_malloc(&d_bad, sizeof(unsigned)) != cudaSuccess) {
     cudaGetLastError();
-    if (d_off) cudaFree(d_off);
-    if (d_bad) cudaFree(d_bad);
+    if (d_off) pgm::dev_free(d_off);
+    if (d_bad) pgm::dev_free(d_bad);
     pgm::set_error("pgm_batch_create: device allocation failed");
     return fail(PGM_ENOMEM);
   }
@@ -455,8 +455,8 @@ pgm_status pgm_batch_create(int32_t G, const int64_t* vtx_off, const int64_t* ro
   }
   cudaMemcpyAsync(&hbad, d_bad, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
   cudaError_t e = cudaStreamSynchronize(s);
-  cudaFree(d_off);
-  cudaFree(d_bad);
+  pgm::dev_free(d_off);
+  pgm::dev_free(d_bad);
   if (e != cudaSuccess) {
     pgm::set_error("pgm_batch_create: %s", cudaGetErrorString(e));
     return fail(PGM_ECUDA);

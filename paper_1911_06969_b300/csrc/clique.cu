@@ -584,13 +584,13 @@ static pgm_status list_kcliques_to(pgm_graph* g, int32_t k, int32_t* out, int64_
   if (k == 1 || k == 2) {
     // n or m rows: no larger than the graph itself
     int32_t* tmp = nullptr;
-    PGM_TRY_CUDA(cudaMalloc(&tmp, (size_t)total * k * sizeof(int32_t)));
+    PGM_TRY_CUDA(pgm::dev_malloc(&tmp, (size_t)total * k * sizeof(int32_t)));
     st = pgm::list_small(G, k, tmp);
     if (st == PGM_OK && cudaMemcpyAsync(out, tmp, (size_t)total * k * sizeof(int32_t), cudaMemcpyDeviceToHost,
                                         G.stream) != cudaSuccess)
       st = PGM_ECUDA;
     if (cudaStreamSynchronize(G.stream) != cudaSuccess && st == PGM_OK) st = PGM_ECUDA;
-    cudaFree(tmp);
+    pgm::dev_free(tmp);
     if (st == PGM_ECUDA) pgm::set_error("%s: copy to the host failed: %s", name, cudaGetErrorString(cudaGetLastError()));
     return st;
   }

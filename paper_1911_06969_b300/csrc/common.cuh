@@ -77,6 +77,25 @@ pgm_status seed_counts(unsigned long long* dev, int n, cudaStream_t s);
 int num_sms();            // SM count of the current device
 int device_id();
 
+// ----------------------------------------------------------- device memory
+// All device memory of the library (graphs, workspaces, scratch) comes from
+// a stream-ordered pool of its own per device, which keeps up to
+// kPoolKeepBytes of freed memory mapped: building and dropping graph
+// handles, orientations and workspaces call after call then costs no
+// mapping work (dropping an R-MAT 21 handle: 0.4 ms of cudaFree before,
+// 0.02 ms from the pool).  dev_malloc returns memory that every
+// stream may use (the allocation is complete on return); dev_free waits for
+// the device like cudaFree, then returns the block to the pool.  An
+// allocation that fails is retried once after the pool's cached memory is
+// released.
+constexpr uint64_t kPoolKeepBytes = (uint64_t)8 << 30;
+cudaError_t dev_malloc(void** p, size_t bytes);
+cudaError_t dev_free(void* p);
+template <typename T>
+cudaError_t dev_malloc(T** p, size_t bytes) {
+  return dev_malloc(reinterpret_cast<void**>(p), bytes);
+}
+
 // ------------------------------------------------------------ device array
 // Grow-only device buffer owned by a handle; never shrinks until freed.
 template <typename T>
@@ -85,22 +104,22 @@ struct DevArr {
   size_t cap = 0;  // elements
   pgm_status reserve(size_t n) {
     if (n <= cap && p) return PGM_OK;
-    if (p) cudaFree(p);
+    if (p) dev_free(p);
     p = nullptr;
     cap = 0;
     size_t want = n ? n : 1;
-    cudaError_t e = cudaMalloc(&p, want * sizeof(T));
+    cudaError_t e = dev_malloc(&p, want * sizeof(T));
     if (e != cudaSuccess) {
       p = nullptr;
       cudaGetLastError();
-      set_error("cudaMalloc of %zu bytes failed: %s", want * sizeof(T), cudaGetErrorString(e));
+      set_error("device allocation of %zu bytes failed: %s", want * sizeof(T), cudaGetErrorString(e));
       return PGM_ENOMEM;
     }
     cap = want;
     return PGM_OK;
   }
   void release() {
-    if (p) cudaFree(p);
+    if (p) dev_free(p);
     p = nullptr;
     cap = 0;
   }
@@ -234,7 +253,7 @@ struct HostSink {
     cap_rows = rows;
     PGM_TRY_CUDA(cudaStreamCreateWithFlags(&copy, cudaStreamNonBlocking));
     for (int b = 0; b < 2; b++) {
-      PGM_TRY_CUDA(cudaMalloc(&buf[b], (size_t)rows * k * sizeof(int32_t)));
+      PGM_TRY_CUDA(dev_malloc(&buf[b], (size_t)rows * k * sizeof(int32_t)));
       PGM_TRY_CUDA(cudaEventCreateWithFlags(&filled[b], cudaEventDisableTiming));
       PGM_TRY_CUDA(cudaEventCreateWithFlags(&done[b], cudaEventDisableTiming));
     }
@@ -268,7 +287,7 @@ struct HostSink {
   void release() {
     if (copy) cudaStreamSynchronize(copy);
     for (int b = 0; b < 2; b++) {
-      if (buf[b]) cudaFree(buf[b]);
+      if (buf[b]) dev_free(buf[b]);
       if (filled[b]) cudaEventDestroy(filled[b]);
       if (done[b]) cudaEventDestroy(done[b]);
       buf[b] = nullptr;

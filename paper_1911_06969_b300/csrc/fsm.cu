@@ -888,12 +888,12 @@ static pgm_status graph_set_labels(Graph& g, const int32_t* labels) {
     centres.push_back(v);
     wprefix.push_back(wprefix.back() + d * (d - 1) / 2);
   }
-  if (g.wedge_centres) cudaFree(g.wedge_centres);
-  if (g.wedge_prefix) cudaFree(g.wedge_prefix);
+  if (g.wedge_centres) pgm::dev_free(g.wedge_centres);
+  if (g.wedge_prefix) pgm::dev_free(g.wedge_prefix);
   g.wedge_centres = nullptr;
   g.wedge_prefix = nullptr;
-  PGM_TRY_CUDA(cudaMalloc(&g.wedge_centres, std::max<size_t>(centres.size(), 1) * sizeof(int32_t)));
-  PGM_TRY_CUDA(cudaMalloc(&g.wedge_prefix, wprefix.size() * sizeof(int64_t)));
+  PGM_TRY_CUDA(pgm::dev_malloc(&g.wedge_centres, std::max<size_t>(centres.size(), 1) * sizeof(int32_t)));
+  PGM_TRY_CUDA(pgm::dev_malloc(&g.wedge_prefix, wprefix.size() * sizeof(int64_t)));
   if (!centres.empty())
     PGM_TRY_CUDA(cudaMemcpyAsync(g.wedge_centres, centres.data(), centres.size() * sizeof(int32_t),
                                  cudaMemcpyHostToDevice, g.stream));
@@ -902,8 +902,8 @@ static pgm_status graph_set_labels(Graph& g, const int32_t* labels) {
   g.n_wedge_centres = (int64_t)centres.size();
   g.n_wedges = wprefix.back();
   const size_t bytes = (size_t)std::max<int32_t>(g.n, 1) * sizeof(int32_t);
-  if (!g.labels) PGM_TRY_CUDA(cudaMalloc(&g.labels, bytes));
-  if (!g.label_rank) PGM_TRY_CUDA(cudaMalloc(&g.label_rank, bytes));
+  if (!g.labels) PGM_TRY_CUDA(pgm::dev_malloc(&g.labels, bytes));
+  if (!g.label_rank) PGM_TRY_CUDA(pgm::dev_malloc(&g.label_rank, bytes));
   if (g.n > 0) {
     PGM_TRY_CUDA(cudaMemcpyAsync(g.labels, labels, (size_t)g.n * sizeof(int32_t), cudaMemcpyHostToDevice, g.stream));
     PGM_TRY_CUDA(cudaMemcpyAsync(g.label_rank, rank.data(), (size_t)g.n * sizeof(int32_t), cudaMemcpyHostToDevice,

@@ -78,49 +78,90 @@ __global__ void rowptr_kernel(int32_t n, const int64_t* __restrict__ rp64, int64
 
 // Orientation, pass 1 (one warp per vertex): out-degree per vertex, one
 // keep flag per arc and the largest out-degree (atomicMax into *dmax).
-__global__ void orient_count_kernel(int32_t n, const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
-                                    uint32_t* __restrict__ outdeg, uint8_t* __restrict__ keep,
-                                    unsigned long long* __restrict__ dmax) {
+// Orientation, arc-parallel (per-vertex warps left the R-MAT hubs, tens of
+// thousands of arcs each, as a long tail).  Arcs are taken in words of 32;
+// a warp owns kOrientWords consecutive words, finds the source of its first
+// arc by binary search in rp and carries it along; each lane walks from the
+// word's first source to its own arc's source (the arcs of a vertex are
+// contiguous).  orient_mask_kernel writes the keep flags of each word as a
+// bit mask and its population count; an exclusive scan of the counts gives
+// every kept arc its DAG position (word offset + rank within the word).
+constexpr int kOrientWords = 64;
+
+__global__ void __launch_bounds__(256) orient_mask_kernel(int32_t n, int64_t narcs, const int32_t* __restrict__ rp,
+                                                          const int32_t* __restrict__ col, uint32_t* __restrict__ mask,
+                                                          uint32_t* __restrict__ cnt) {
   const int lane = threadIdx.x & 31;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  uint32_t cmax = 0;
-  for (int64_t u = warp; u < n; u += nwarps) {
-    const int32_t a0 = rp[u], a1 = rp[u + 1];
-    const int32_t du = a1 - a0;
-    uint32_t c = 0;
-    for (int32_t a = a0; a < a1; a += 32) {
-      bool k = false;
-      if (a + lane < a1) {
-        const int32_t v = col[a + lane];
-        k = keep_arc((int32_t)u, du, v, rp[v + 1] - rp[v]);
-        keep[a + lane] = k ? 1 : 0;
+  const int64_t nwords = (narcs + 31) >> 5;
+  for (int64_t w0 = warp * kOrientWords; w0 < nwords; w0 += nwarps * kOrientWords) {
+    // source of arc 32 w0: the largest u with rp[u] <= 32 w0 (rp[0] = 0)
+    int32_t u = 0;
+    if (lane == 0) {
+      int32_t lo = 0, hi = n - 1;
+      const int64_t a0 = w0 << 5;
+      while (lo < hi) {
+        const int32_t mid = lo + ((hi - lo + 1) >> 1);
+        if (rp[mid] <= a0) lo = mid; else hi = mid - 1;
       }
-      c += __popc(__ballot_sync(kFull, k));
+      u = lo;
     }
-    if (lane == 0) outdeg[u] = c;
-    cmax = max(cmax, c);
+    u = __shfl_sync(kFull, u, 0);
+    const int64_t w1 = min(w0 + kOrientWords, nwords);
+    for (int64_t w = w0; w < w1; w++) {
+      const int64_t a = (w << 5) + lane;
+      bool k = false;
+      int32_t su = u;
+      if (a < narcs) {
+        while (rp[su + 1] <= a) su++;  // su < n: rp[n] = narcs > a
+        const int32_t v = col[a];
+        k = keep_arc(su, rp[su + 1] - rp[su], v, rp[v + 1] - rp[v]);
+      }
+      const unsigned bal = __ballot_sync(kFull, k);
+      if (lane == 0) {
+        mask[w] = bal;
+        cnt[w] = __popc(bal);
+      }
+      u = __shfl_sync(kFull, su, 31);  // the last lane's source starts the next word
+    }
   }
-  if (lane == 0 && cmax) atomicMax(dmax, (unsigned long long)cmax);
 }
 
-// Orientation, pass 2: compact the kept arcs (keep flags of pass 1).
-__global__ void orient_write_kernel(int32_t n, const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
-                                    const uint8_t* __restrict__ keep, const int64_t* __restrict__ dag_off,
-                                    int32_t* __restrict__ dag_col) {
-  const int lane = threadIdx.x & 31;
-  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t u = warp; u < n; u += nwarps) {
-    const int32_t a0 = rp[u], a1 = rp[u + 1];
-    int64_t w = dag_off[u];
-    for (int32_t a = a0; a < a1; a += 32) {
-      const bool k = a + lane < a1 && keep[a + lane];
-      const unsigned b = __ballot_sync(kFull, k);
-      if (k) dag_col[w + __popc(b & ((1u << lane) - 1u))] = col[a + lane];
-      w += __popc(b);
-    }
+// DAG position of arc a: kept arcs before it
+__device__ __forceinline__ int64_t orient_pos(const uint32_t* mask, const int64_t* off, int64_t a) {
+  const int64_t w = a >> 5;
+  const int b = (int)(a & 31);
+  return off[w] + (b ? __popc(mask[w] & ((1u << b) - 1u)) : 0);
+}
+
+// The kept arcs into dag_col (thread per arc), and dag_rp plus the largest
+// out-degree (thread per vertex, u = n gives the end pointer).
+__global__ void __launch_bounds__(256) orient_write_kernel(int64_t narcs, const int32_t* __restrict__ col,
+                                                           const uint32_t* __restrict__ mask,
+                                                           const int64_t* __restrict__ off,
+                                                           int32_t* __restrict__ dag_col) {
+  for (int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; a < narcs; a += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t w = a >> 5;
+    const int b = (int)(a & 31);
+    const uint32_t m = mask[w];
+    if ((m >> b) & 1u) dag_col[off[w] + __popc(m & ((1u << b) - 1u))] = col[a];
   }
+}
+
+__global__ void __launch_bounds__(256) orient_rows_kernel(int32_t n, const int32_t* __restrict__ rp,
+                                                          const uint32_t* __restrict__ mask,
+                                                          const int64_t* __restrict__ off,
+                                                          int32_t* __restrict__ dag_rp,
+                                                          unsigned long long* __restrict__ dmax) {
+  unsigned cmax = 0;
+  for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u <= n; u += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t p0 = orient_pos(mask, off, rp[u]);
+    dag_rp[u] = (int32_t)p0;
+    if (u < n) cmax = max(cmax, (unsigned)(orient_pos(mask, off, rp[u + 1]) - p0));
+  }
+  cmax = __reduce_max_sync(kFull, cmax);
+  if ((threadIdx.x & 31) == 0 && cmax) atomicMax(dmax, (unsigned long long)cmax);
 }
 
 __global__ void narrow_kernel(const int64_t* __restrict__ in, int32_t* __restrict__ out, int64_t len) {
@@ -215,20 +256,20 @@ void graph_free(Graph& g) {
       graph_free(*r);
       r.reset();
     }
-  if (g.rp) cudaFree(g.rp);
-  if (g.col) cudaFree(g.col);
-  if (g.dag_rp) cudaFree(g.dag_rp);
-  if (g.dag_col) cudaFree(g.dag_col);
-  if (g.gid) cudaFree(g.gid);
-  if (g.up) cudaFree(g.up);
-  if (g.src) cudaFree(g.src);
-  if (g.rev) cudaFree(g.rev);
-  if (g.hub_idx) cudaFree(g.hub_idx);
-  if (g.labels) cudaFree(g.labels);
-  if (g.label_rank) cudaFree(g.label_rank);
-  if (g.wedge_centres) cudaFree(g.wedge_centres);
-  if (g.wedge_prefix) cudaFree(g.wedge_prefix);
-  if (g.hub_bits) cudaFree(g.hub_bits);
+  if (g.rp) pgm::dev_free(g.rp);
+  if (g.col) pgm::dev_free(g.col);
+  if (g.dag_rp) pgm::dev_free(g.dag_rp);
+  if (g.dag_col) pgm::dev_free(g.dag_col);
+  if (g.gid) pgm::dev_free(g.gid);
+  if (g.up) pgm::dev_free(g.up);
+  if (g.src) pgm::dev_free(g.src);
+  if (g.rev) pgm::dev_free(g.rev);
+  if (g.hub_idx) pgm::dev_free(g.hub_idx);
+  if (g.labels) pgm::dev_free(g.labels);
+  if (g.label_rank) pgm::dev_free(g.label_rank);
+  if (g.wedge_centres) pgm::dev_free(g.wedge_centres);
+  if (g.wedge_prefix) pgm::dev_free(g.wedge_prefix);
+  if (g.hub_bits) pgm::dev_free(g.hub_bits);
   g.rp = g.col = g.dag_rp = g.dag_col = g.gid = g.up = g.src = g.hub_idx = g.rev = nullptr;
   g.hub_bits = nullptr;
   g.labels = nullptr;
@@ -285,8 +326,8 @@ pgm_status graph_upload(Graph& g, int32_t n, const int64_t* rowptr, const int32_
     return narcs < 0 ? PGM_EINVAL : PGM_EUNSUPPORTED;
   }
   g.narcs = narcs;
-  PGM_TRY_CUDA(cudaMalloc(&g.rp, ((size_t)n + 1) * sizeof(int32_t)));
-  PGM_TRY_CUDA(cudaMalloc(&g.col, (size_t)std::max<int64_t>(narcs, 1) * sizeof(int32_t)));
+  PGM_TRY_CUDA(pgm::dev_malloc(&g.rp, ((size_t)n + 1) * sizeof(int32_t)));
+  PGM_TRY_CUDA(pgm::dev_malloc(&g.col, (size_t)std::max<int64_t>(narcs, 1) * sizeof(int32_t)));
   const int64_t* rp64 = rowptr;
   if (!rowptr_on_device) {
     PGM_TRY(g.ws.off[0].reserve((size_t)n + 1));
@@ -381,44 +422,49 @@ pgm_status graph_orient(Graph& g) {
     set_error("orient: odd number of arcs (input not symmetric)");
     return PGM_EINVAL;
   }
-  if (!g.dag_rp) PGM_TRY_CUDA(cudaMalloc(&g.dag_rp, ((size_t)n + 1) * sizeof(int32_t)));
-  if (!g.dag_col) PGM_TRY_CUDA(cudaMalloc(&g.dag_col, (size_t)std::max<int64_t>(m, 1) * sizeof(int32_t)));
-  PGM_TRY(g.ws.cnt[0].reserve((size_t)n + 1));
-  PGM_TRY(g.ws.off[0].reserve((size_t)n + 1));
+  if (!g.dag_rp) PGM_TRY_CUDA(pgm::dev_malloc(&g.dag_rp, ((size_t)n + 1) * sizeof(int32_t)));
+  if (!g.dag_col) PGM_TRY_CUDA(pgm::dev_malloc(&g.dag_col, (size_t)std::max<int64_t>(m, 1) * sizeof(int32_t)));
+  const int64_t nwords = (g.narcs + 31) / 32;
+  PGM_TRY(g.ws.cnt[0].reserve((size_t)std::max<int64_t>(nwords, 1)));
+  PGM_TRY(g.ws.off[0].reserve((size_t)nwords + 1));
   PGM_TRY(g.ws.ctr.reserve(16));
-  DevArr<uint8_t> keep;  // one flag per arc, freed on return
-  PGM_TRY(keep.reserve((size_t)std::max<int64_t>(g.narcs, 1)));
+  DevArr<uint32_t> mask;  // keep flags, one word per 32 arcs, freed on return
+  PGM_TRY(mask.reserve((size_t)std::max<int64_t>(nwords, 1)));
   struct Free {
-    DevArr<uint8_t>& k;
+    DevArr<uint32_t>& k;
     ~Free() { k.release(); }
-  } free_keep{keep};
+  } free_mask{mask};
   unsigned long long* dmax_dev = g.ws.ctr.p + 3;
   PGM_TRY_CUDA(cudaMemsetAsync(dmax_dev, 0, sizeof(unsigned long long), s));
   Profiler& prof = profiler();
   int id = prof.begin("orient", 1);
-  if (n > 0) {
-    orient_count_kernel<<<warp_grid(n, 256), 256, 0, s>>>(n, g.rp, g.col, g.ws.cnt[0].p, keep.p, dmax_dev);
+  const int grid = std::max(1, num_sms() * 8);
+  if (g.narcs > 0) {
+    const int64_t ranges = (nwords + kOrientWords - 1) / kOrientWords;
+    orient_mask_kernel<<<(int)std::min<int64_t>(grid, (ranges + 7) / 8), 256, 0, s>>>(n, g.narcs, g.rp, g.col,
+                                                                                      mask.p, g.ws.cnt[0].p);
     PGM_CHECK_LAUNCH();
   }
-  PGM_TRY(exclusive_scan(g.ws.cnt[0].p, n, g.ws.off[0].p, g.ws, s));
+  PGM_TRY(exclusive_scan(g.ws.cnt[0].p, nwords, g.ws.off[0].p, g.ws, s));
   int64_t kept = 0;
-  unsigned long long dd = 0;
-  PGM_TRY_CUDA(cudaMemcpyAsync(&kept, g.ws.off[0].p + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-  PGM_TRY_CUDA(cudaMemcpyAsync(&dd, dmax_dev, sizeof(dd), cudaMemcpyDeviceToHost, s));
+  PGM_TRY_CUDA(cudaMemcpyAsync(&kept, g.ws.off[0].p + nwords, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
   PGM_TRY_CUDA(cudaStreamSynchronize(s));
   if (kept != m) {
     // not symmetric: the kept-arc count differs from m; refuse before writing
     set_error("orient: kept %lld arcs, expected %lld (input not symmetric?)", (long long)kept, (long long)m);
     return PGM_EINVAL;
   }
-  if (n > 0) {
-    orient_write_kernel<<<warp_grid(n, 256), 256, 0, s>>>(n, g.rp, g.col, keep.p, g.ws.off[0].p, g.dag_col);
+  if (g.narcs > 0) {
+    orient_write_kernel<<<(int)std::min<int64_t>(grid, (g.narcs + 255) / 256), 256, 0, s>>>(
+        g.narcs, g.col, mask.p, g.ws.off[0].p, g.dag_col);
     PGM_CHECK_LAUNCH();
   }
-  narrow_kernel<<<std::max(1, std::min(num_sms() * 8, (int)((n + 256) / 256))), 256, 0, s>>>(
-      g.ws.off[0].p, g.dag_rp, (int64_t)n + 1);
+  orient_rows_kernel<<<(int)std::min<int64_t>(grid, ((int64_t)n + 256) / 256), 256, 0, s>>>(
+      n, g.rp, mask.p, g.ws.off[0].p, g.dag_rp, dmax_dev);
   PGM_CHECK_LAUNCH();
   prof.end(id, (double)n, 8.0 * (double)g.narcs);
+  unsigned long long dd = 0;
+  PGM_TRY_CUDA(cudaMemcpyAsync(&dd, dmax_dev, sizeof(dd), cudaMemcpyDeviceToHost, s));
   PGM_TRY_CUDA(cudaStreamSynchronize(s));
   g.dag_dmax = (int64_t)dd;
   g.h_dag_rp.clear();  // host copy made on first use (graph_host_dag_rp)
@@ -439,10 +485,10 @@ pgm_status graph_prepare_motifs(Graph& g) {
   PGM_TRY(graph_host_rp(g));
   cudaStream_t s = g.stream;
   const int32_t n = g.n;
-  PGM_TRY_CUDA(cudaMalloc(&g.up, ((size_t)n + 1) * sizeof(int32_t)));
-  PGM_TRY_CUDA(cudaMalloc(&g.src, (size_t)std::max<int64_t>(g.narcs, 1) * sizeof(int32_t)));
-  PGM_TRY_CUDA(cudaMalloc(&g.rev, (size_t)std::max<int64_t>(g.narcs, 1) * sizeof(int32_t)));
-  PGM_TRY_CUDA(cudaMalloc(&g.hub_idx, ((size_t)n + 1) * sizeof(int32_t)));
+  PGM_TRY_CUDA(pgm::dev_malloc(&g.up, ((size_t)n + 1) * sizeof(int32_t)));
+  PGM_TRY_CUDA(pgm::dev_malloc(&g.src, (size_t)std::max<int64_t>(g.narcs, 1) * sizeof(int32_t)));
+  PGM_TRY_CUDA(pgm::dev_malloc(&g.rev, (size_t)std::max<int64_t>(g.narcs, 1) * sizeof(int32_t)));
+  PGM_TRY_CUDA(pgm::dev_malloc(&g.hub_idx, ((size_t)n + 1) * sizeof(int32_t)));
   PGM_TRY_CUDA(cudaMemsetAsync(g.hub_idx, 0xff, ((size_t)n + 1) * sizeof(int32_t), s));
   if (n > 0) {
     const int blocks = std::max(1, std::min(num_sms() * 8, (n + 255) / 256));
@@ -466,10 +512,10 @@ pgm_status graph_prepare_motifs(Graph& g) {
   if (nh > 0) {
     std::vector<int32_t> hubs(nh), idx(nh);
     for (int32_t h = 0; h < nh; h++) hubs[h] = cand[h].second;
-    PGM_TRY_CUDA(cudaMalloc(&g.hub_bits, (size_t)nh * g.hub_words * sizeof(uint32_t)));
+    PGM_TRY_CUDA(pgm::dev_malloc(&g.hub_bits, (size_t)nh * g.hub_words * sizeof(uint32_t)));
     PGM_TRY_CUDA(cudaMemsetAsync(g.hub_bits, 0, (size_t)nh * g.hub_words * sizeof(uint32_t), s));
     int32_t* d_hubs = nullptr;
-    PGM_TRY_CUDA(cudaMalloc(&d_hubs, (size_t)nh * sizeof(int32_t)));
+    PGM_TRY_CUDA(pgm::dev_malloc(&d_hubs, (size_t)nh * sizeof(int32_t)));
     PGM_TRY_CUDA(cudaMemcpyAsync(d_hubs, hubs.data(), (size_t)nh * sizeof(int32_t), cudaMemcpyHostToDevice, s));
     hub_bits_kernel<<<std::min(nh, num_sms() * 4), 256, 0, s>>>(d_hubs, nh, g.rp, g.col, g.hub_bits,
                                                                 g.hub_words);
@@ -479,7 +525,7 @@ pgm_status graph_prepare_motifs(Graph& g) {
     for (int32_t h = 0; h < nh; h++)
       PGM_TRY_CUDA(cudaMemcpyAsync(g.hub_idx + hubs[h], &idx[h], sizeof(int32_t), cudaMemcpyHostToDevice, s));
     PGM_TRY_CUDA(cudaStreamSynchronize(s));
-    cudaFree(d_hubs);
+    pgm::dev_free(d_hubs);
   }
   g.nhubs = nh;
   PGM_TRY_CUDA(cudaStreamSynchronize(s));

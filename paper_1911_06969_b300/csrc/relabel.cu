@@ -80,9 +80,9 @@ pgm_status build_relabeled(Graph& g, bool descending, Graph& r) {
   PGM_TRY(order.reserve(nn));
   PGM_TRY(newid.reserve(nn));
   PGM_TRY(deg_new.reserve(nn + 1));
-  PGM_TRY_CUDA(cudaMalloc(&r.rp, ((size_t)n + 1) * sizeof(int32_t)));
-  PGM_TRY_CUDA(cudaMalloc(&r.col, (size_t)std::max<int64_t>(narcs, 1) * sizeof(int32_t)));
-  if (g.gid) PGM_TRY_CUDA(cudaMalloc(&r.gid, nn * sizeof(int32_t)));
+  PGM_TRY_CUDA(pgm::dev_malloc(&r.rp, ((size_t)n + 1) * sizeof(int32_t)));
+  PGM_TRY_CUDA(pgm::dev_malloc(&r.col, (size_t)std::max<int64_t>(narcs, 1) * sizeof(int32_t)));
+  if (g.gid) PGM_TRY_CUDA(pgm::dev_malloc(&r.gid, nn * sizeof(int32_t)));
   int32_t* col_unsorted = nullptr;
   struct Cleanup {
     DevArr<unsigned long long>& a;
@@ -101,7 +101,7 @@ pgm_status build_relabeled(Graph& g, bool descending, Graph& r) {
       e.release();
       f.release();
       t.release();
-      if (cu) cudaFree(cu);
+      if (cu) pgm::dev_free(cu);
     }
   } cleanup{key, key2, val, order, newid, deg_new, tmp, col_unsorted};
   const int blocks = std::max(1, std::min(num_sms() * 8, (int)((n + 255) / 256)));
@@ -120,7 +120,7 @@ pgm_status build_relabeled(Graph& g, bool descending, Graph& r) {
   PGM_TRY(exclusive_scan(deg_new.p, n, r.ws.off[0].p, r.ws, s));
   narrow_rowptr(r.ws.off[0].p, r.rp, (int64_t)n + 1, s);
   if (n > 0 && narcs > 0) {
-    PGM_TRY_CUDA(cudaMalloc(&col_unsorted, (size_t)narcs * sizeof(int32_t)));
+    PGM_TRY_CUDA(pgm::dev_malloc(&col_unsorted, (size_t)narcs * sizeof(int32_t)));
     const int wblocks = std::max(1, std::min(num_sms() * 16, (int)(((int64_t)n * 32 + 255) / 256)));
     relabel_lists_kernel<<<wblocks, 256, 0, s>>>(n, order.p, g.rp, g.col, newid.p, r.rp, col_unsorted);
     PGM_CHECK_LAUNCH();
