@@ -834,6 +834,30 @@ int64_t bitset_scratch_bytes(const Graph& g, int k) {
   return (int64_t)grid_for(fn, 512, smem) * bitset_row_words(g.dag_dmax, k) * 4;
 }
 
+// Streams and events for forking the bucket launches (per thread and
+// device: a call's events must not be recorded by another thread's call).
+constexpr int kForks = kBmBuckets;
+struct ForkStreams {
+  int dev = -1;
+  cudaStream_t s[kForks] = {};
+  cudaEvent_t ev[1 + kForks] = {};
+};
+
+pgm_status fork_streams(ForkStreams** out) {
+  thread_local ForkStreams F[8];
+  const int dev = device_id();
+  *out = nullptr;
+  if (dev < 0 || dev >= 8) return PGM_OK;  // no fork: launches stay on the caller's stream
+  ForkStreams& f = F[dev];
+  if (f.dev != dev) {
+    for (int i = 0; i < kForks; i++) PGM_TRY_CUDA(cudaStreamCreateWithFlags(&f.s[i], cudaStreamNonBlocking));
+    for (int i = 0; i <= kForks; i++) PGM_TRY_CUDA(cudaEventCreateWithFlags(&f.ev[i], cudaEventDisableTiming));
+    f.dev = dev;
+  }
+  *out = &f;
+  return PGM_OK;
+}
+
 // Bitset engine entry: counts k-cliques (k in 3..10) rooted in [v_lo, v_hi).
 // Returns PGM_EUNSUPPORTED when the DAG's largest out-degree would need more
 // than `max_scratch` bytes of row scratch (the caller then uses the
@@ -936,20 +960,39 @@ pgm_status count_kcliques_bitset(Graph& g, Workspace& ws, cudaStream_t s, int k,
   B.clevels = clevels;
   int wgrid = grid_for(warp_fn, 256, 0);
   wgrid = (int)std::max<int64_t>(1, std::min<int64_t>(wgrid, ((nv + kBmGrab - 1) / kBmGrab + 7) / 8));
+  // The buckets depend on the warp kernel (it fills their vertex lists) but
+  // not on one another: outside a stream capture or a plan recording they
+  // run on forked streams, so that one bucket's tail overlaps the next.
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  PGM_TRY_CUDA(cudaStreamIsCapturing(s, &cap));
+  ForkStreams* F = nullptr;
+  if (cap == cudaStreamCaptureStatusNone && !current_plan()) PGM_TRY(fork_streams(&F));
   Profiler& prof = profiler();
   int id = prof.begin("bitset_count", 3);
   if (nv > 0) {
     void* wargv[] = {&B};
     PGM_TRY_CUDA(cudaLaunchKernel(warp_fn, dim3(wgrid), dim3(256), wargv, 0, s));
     PGM_CHECK_LAUNCH();
+    if (F) PGM_TRY_CUDA(cudaEventRecord(F->ev[0], s));
     // largest rows first, so that the short tail of each launch is cheap
+    int nf = 0;
     for (int b = kBmBuckets - 1; b >= 0; b--) {
       if (!used[b]) continue;  // bucket unused at this shared-memory limit
       const Kern& K = kern[b];
       void* argv[] = {&B, &b};
-      PGM_TRY_CUDA(cudaLaunchKernel(K.fn, dim3(K.grid), dim3(K.threads), argv, K.smem, s));
+      cudaStream_t t = s;
+      if (F && nf < kForks) {
+        t = F->s[nf];
+        PGM_TRY_CUDA(cudaStreamWaitEvent(t, F->ev[0], 0));
+      }
+      PGM_TRY_CUDA(cudaLaunchKernel(K.fn, dim3(K.grid), dim3(K.threads), argv, K.smem, t));
       PGM_CHECK_LAUNCH();
+      if (t != s) {
+        PGM_TRY_CUDA(cudaEventRecord(F->ev[1 + nf], t));
+        nf++;
+      }
     }
+    for (int i = 0; i < nf; i++) PGM_TRY_CUDA(cudaStreamWaitEvent(s, F->ev[1 + i], 0));
   }
   prof.end(id, (double)arcs, 0.0);
   unsigned long long h[kBmSlots];
