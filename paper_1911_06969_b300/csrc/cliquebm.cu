@@ -977,7 +977,8 @@ pgm_status count_kcliques_bitset(Graph& g, Workspace& ws, cudaStream_t s, int k,
     // largest rows first, so that the short tail of each launch is cheap
     int nf = 0;
     for (int b = kBmBuckets - 1; b >= 0; b--) {
-      if (!used[b]) continue;  // bucket unused at this shared-memory limit
+      if (!used[b]) continue;               // bucket unused at this shared-memory limit
+      if (g.dag_dmax <= lo[b]) continue;    // no out-degree reaches the bucket
       const Kern& K = kern[b];
       void* argv[] = {&B, &b};
       cudaStream_t t = s;
