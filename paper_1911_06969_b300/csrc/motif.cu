@@ -123,9 +123,11 @@ __device__ __forceinline__ bool member(const int32_t* L, int len, int hb, const 
 // ------------------------------------------------------ level 2 -> 3 / 3-motif
 // Entries j0..j0+31 of v0's segment A (length s).  For entry j (v1 = A[j])
 // scan N(v1): x > v0 and not in A -> f2=1 child; x in A and x > v1 -> the
-// f2=0 child x is a triangle (a12 = 1).
+// f2=0 child x is a triangle (a12 = 1).  Membership in A comes from v0's hub
+// bitmap when it has one (hA >= 0: A = N(v0) above v0), the binary search
+// then only placing the triangles.
 template <int MODE>
-__device__ __forceinline__ void l2_batch(const MotifArgs& P, const int32_t* A, int s, int j0,
+__device__ __forceinline__ void l2_batch(const MotifArgs& P, const int32_t* A, int s, int hA, int j0,
                                          int32_t v0, int64_t arc0, int lane, uint32_t* wcnt,
                                          long long (&c)[2], unsigned long long& seen) {
   const int j = j0 + lane;
@@ -174,11 +176,16 @@ __device__ __forceinline__ void l2_batch(const MotifArgs& P, const int32_t* A, i
       if (x > v0) {
         bool inA = false;
         if (x >= amin && x <= amax) {
-          xi = lower_bound_dev(A, s, x);
-          inA = xi < s && A[xi] == x;
+          if (hA >= 0) {
+            inA = member(A, s, hA, P, x);
+          } else {
+            xi = lower_bound_dev(A, s, x);
+            inA = xi < s && A[xi] == x;
+          }
         }
         child = !inA;
         tri = inA && x > v1q;
+        if (MODE == mWrite && tri && hA >= 0) xi = lower_bound_dev(A, s, x);
       }
     }
     if (MODE == mSum) {
@@ -308,7 +315,7 @@ __device__ __forceinline__ void l2_any_batch(const MotifArgs& P, const int32_t* 
                                              int32_t v0, int64_t arc0, int lane, uint32_t* wcnt,
                                              long long (&c)[2], unsigned long long& seen) {
   if (MODE == mWrite)
-    l2_batch<MODE>(P, A, s, j0, v0, arc0, lane, wcnt, c, seen);
+    l2_batch<MODE>(P, A, s, hA, j0, v0, arc0, lane, wcnt, c, seen);
   else
     l2_count_batch<MODE>(P, A, s, hA, j0, v0, arc0, lane, wcnt, c, seen);
 }
