@@ -89,6 +89,11 @@ struct MotifArgs {
   // written by the level-3 inspection, read by the last level (memoised
   // per level-2 edge, Sec. 4.2, instead of recomputed per level-3 entry)
   uint2* tri;
+  // exclusive prefix sums over the same arcs of tri.y and of (|N(v2) above
+  // v0| - tri.x) for arcs above v0 (0 elsewhere): the base region sizes of
+  // all f2 = 0 children of an edge in O(1) (motif_l3_edge)
+  const int64_t* py;
+  const int64_t* pz;
   unsigned long long* carry;  // wraps of the count accumulators (add_count)
   int b_side_min;  // last level: edges with at least this many f2 = 0 children find them from B's side
   // lengths for the checked index sites (PGM_DEBUG builds)
@@ -465,6 +470,25 @@ __global__ void __launch_bounds__(512, 2) motif_l2_block(MotifArgs P) {
   if (lane == 0 && seen) atomicAdd(P.stat, seen);
 }
 
+// Per-arc terms of the f2 = 0 base region sizes, for arcs a = (v0, v2) with
+// v2 > v0: tri.y, and |N(v2) & (v0, inf)| - tri.x (v2's neighbours above v0
+// outside A); 0 for arcs below v0.  Scanned into py / pz.
+__global__ void motif_arc_terms(MotifArgs P, int64_t E, uint32_t* __restrict__ ty, uint32_t* __restrict__ tz) {
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < E; k += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t a = P.a_base + k;
+    const int32_t v0 = P.src[a], v2 = P.col[a];
+    uint32_t y = 0, z = 0;
+    if (v2 > v0) {
+      const uint2 tr = P.tri[k];
+      const int32_t sl = P.rp[v2 + 1] - (P.rev[a] + 1);
+      y = tr.y;
+      z = (uint32_t)(sl - (int32_t)tr.x);
+    }
+    ty[k] = y;
+    tz[k] = z;
+  }
+}
+
 // ------------------------------------------------------------- level 3 (last)
 
 // Per-warp filters of the last level: one-hash bitmaps of at most kMFilterW
@@ -757,7 +781,49 @@ __global__ void __launch_bounds__(kML3Threads, 3) motif_l3_edge(MotifArgs P) {
         }
       };
       const bool from_b = nf0 >= P.b_side_min;
-      for (int64_t next = cb; next < ce; next += 32) {
+      if (from_b) {
+        // Base region sizes of all f2 = 0 children (v2 = A[idx], j1 < idx < s)
+        // in closed form instead of per child: the sums over idx of the three
+        // sizes below come from the prefix arrays (tri.y, |N(v2) above v0| -
+        // tri.x) and from I (sum of |I & (v2, inf)| = sum over w in I above v1
+        // of the children below w); the a12 = 1 children (v2 in I, above v1)
+        // are taken out of the a12 = 0 sums and added with their own folding.
+        long long sI = 0, t1 = 0, t24 = 0, t35 = 0;
+        for (int k0 = 0; k0 < ni; k0 += 32) {
+          const int k = k0 + lane;
+          if (k < ni) {
+            const int32_t w = I[k];
+            if (w > v1) {
+              const int ra = lower_bound_dev(A, s, w);  // w = A[ra]
+              sI += ra - j1 - 1;
+              const int64_t a2 = (int64_t)u0 + ra;
+              if (PGM_IDX_OK(a2 - P.a_base, P.n_arc_slots)) {
+                const uint2 tr = P.tri[a2 - P.a_base];
+                const int sl = P.rp[w + 1] - (P.rev[a2] + 1);
+                const long long igt = ni - k - 1;  // |I & (w, inf)|
+                t1 += (long long)(s - ra - 1) - igt - (long long)tr.y;
+                t24 += (long long)(nb - ni) + sl - (long long)tr.x;
+                t35 += igt + (long long)tr.y;
+              }
+            }
+          }
+        }
+        c[0] += -sI - t1;
+        c[1] += -t24;
+        c[2] += sI - t35 + t1 + t24;
+        c[4] += t35;
+        if (lane == 0) {
+          const int64_t lo = (int64_t)u0 + j1 + 1 - P.a_base, hi = (int64_t)u0 + s - P.a_base;
+          if (PGM_IDX_OK(hi, P.n_arc_slots + 1)) {
+            const long long sy = P.py[hi] - P.py[lo], sz = P.pz[hi] - P.pz[lo];
+            c[0] += (long long)nf0 * (nf0 - 1) / 2 - sy;
+            c[1] += (long long)nf0 * (nb - ni) + sz;
+            c[2] += sy;
+          }
+        }
+      }
+      // the children loop: f2 = 0 children (unless done above) and f2 = 1 children
+      for (int64_t next = from_b ? cb + nf0 : cb; next < ce; next += 32) {
         int32_t tag0 = 0;
         int len = 0, start = 0, tag1 = 0;
         {
@@ -986,6 +1052,8 @@ struct MotifRun {
     P.hub_words = g.hub_words;
     P.rev = g.rev;
     P.tri = ws.tri.p;
+    P.py = ws.off[4].p;
+    P.pz = ws.off[5].p;
     P.carry = ctr() + kCarrySlot;
     P.narcs = g.narcs;
     P.n_arc_slots = g.h_rp[v_hi] - g.h_rp[v_lo];
@@ -1081,10 +1149,25 @@ struct MotifRun {
     PGM_TRY(ws.cnt[2].reserve((size_t)E));
     PGM_TRY(ws.off[2].reserve((size_t)E + 1));
     PGM_TRY(ws.tri.reserve((size_t)E));
+    PGM_TRY(ws.cnt[4].reserve((size_t)E));
+    PGM_TRY(ws.cnt[5].reserve((size_t)E));
+    PGM_TRY(ws.off[4].reserve((size_t)E + 1));
+    PGM_TRY(ws.off[5].reserve((size_t)E + 1));
     PGM_TRY_CUDA(cudaMemsetAsync(ws.cnt[2].p, 0, (size_t)E * sizeof(uint32_t), s));
+    PGM_TRY_CUDA(cudaMemsetAsync(ws.tri.p, 0, (size_t)E * sizeof(uint2), s));
     MotifArgs P = args(v_lo, v_hi);
     P.cnt = ws.cnt[2].p;
     PGM_TRY(launch_l2<mCount>(P, "extend_count"));
+    {
+      // prefix sums of the per-arc terms of the f2 = 0 base region sizes
+      P.a_base = a_lo;
+      P.src = g.src;  // arc sources (set by launch_l3 for the last level; needed here too)
+      motif_arc_terms<<<std::max(1, std::min(num_sms() * 8, (int)((E + 255) / 256))), 256, 0, s>>>(
+          P, E, ws.cnt[4].p, ws.cnt[5].p);
+      PGM_CHECK_LAUNCH();
+      PGM_TRY(exclusive_scan(ws.cnt[4].p, E, ws.off[4].p, ws, s));
+      PGM_TRY(exclusive_scan(ws.cnt[5].p, E, ws.off[5].p, ws, s));
+    }
     {
       int id = profiler().begin("scan", 2);
       PGM_TRY(exclusive_scan(ws.cnt[2].p, E, ws.off[2].p, ws, s));
