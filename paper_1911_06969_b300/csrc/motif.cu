@@ -96,6 +96,10 @@ struct MotifArgs {
   const int64_t* pz;
   unsigned long long* carry;  // wraps of the count accumulators (add_count)
   int b_side_min;  // last level: edges with at least this many f2 = 0 children find them from B's side
+  // (their f2 = 0 children are neither stored in the level-3 list nor read:
+  // motif_l3_pairs finds their common neighbours, motif_l3_edge sums their
+  // base region sizes in closed form); the inspection adds their number here
+  unsigned long long* skipped;
   // lengths for the checked index sites (PGM_DEBUG builds)
   int64_t narcs;        // col, rev, src
   int64_t n_arc_slots;  // cnt, tri (arcs of the launch's vertex range)
@@ -160,6 +164,7 @@ __device__ __forceinline__ void l2_batch(const MotifArgs& P, const int32_t* A, i
       const int jq = j0 + q;
       if (jq >= s) break;
       const int64_t oq = __shfl_sync(kFull, my_off, q);
+      if (s - jq - 1 >= P.b_side_min) continue;  // not stored (see b_side_min)
       for (int i = jq + 1 + lane; i < s; i += 32)
         if (PGM_IDX_OK(oq + (i - jq - 1), P.n_l3)) P.l3[oq + (i - jq - 1)] = (uint32_t)A[i] | kA02;
     }
@@ -205,9 +210,11 @@ __device__ __forceinline__ void l2_batch(const MotifArgs& P, const int32_t* A, i
         const int64_t oq = __shfl_sync(kFull, my_off, q);
         const int jq = j0 + q;
         const uint32_t rq = wcnt[q];
-        const int64_t ic = oq + (s - jq - 1) + rq + __popc(b & from_first & ((1u << lane) - 1u));
+        const bool fbq = s - jq - 1 >= P.b_side_min;  // this edge's f2 = 0 block is not stored
+        const int64_t ic = oq + (fbq ? 0 : s - jq - 1) + rq + __popc(b & from_first & ((1u << lane) - 1u));
         if (child && PGM_IDX_OK(ic, P.n_l3)) P.l3[ic] = (uint32_t)x | kA12;
-        if (tri && PGM_IDX_OK(oq + (xi - jq - 1), P.n_l3)) P.l3[oq + (xi - jq - 1)] = (uint32_t)x | kA02 | kA12;
+        if (tri && !fbq && PGM_IDX_OK(oq + (xi - jq - 1), P.n_l3))
+          P.l3[oq + (xi - jq - 1)] = (uint32_t)x | kA02 | kA12;
       }
       const int qn = __shfl_down_sync(kFull, q, 1);
       const bool last = active && (lane == 31 || t + 1 >= total || qn != q);
@@ -305,10 +312,13 @@ __device__ __forceinline__ void l2_count_batch(const MotifArgs& P, const int32_t
     }
   }
   if (MODE == mCount) {
+    const bool fb = valid && s - j - 1 >= P.b_side_min;  // f2 = 0 children not stored
     if (valid && PGM_IDX_OK(arc0 + j, P.n_arc_slots)) {
-      P.cnt[arc0 + j] = (uint32_t)(s - j - 1) + (uint32_t)nbj - wcnt[lane];
+      P.cnt[arc0 + j] = (fb ? 0u : (uint32_t)(s - j - 1)) + (uint32_t)nbj - wcnt[lane];
       P.tri[arc0 + j] = make_uint2(wcnt[lane], wcnt[32 + lane]);
     }
+    const unsigned long long sk = warp_sum((unsigned long long)(fb ? s - j - 1 : 0));
+    if (lane == 0 && sk) atomicAdd(P.skipped, sk);
     __syncwarp();
   }
 }
@@ -674,8 +684,10 @@ __global__ void __launch_bounds__(kML3Threads, 3) motif_l3_edge(MotifArgs P) {
       const int64_t rel = a - P.a_base;
       const int64_t cb = P.off[rel] - P.off_shift;
       const int64_t ce = P.off[rel + 1] - P.off_shift;
-      if (ce <= cb) continue;  // arcs to lower neighbours and childless edges
       const int32_t v0 = P.src[a], v1 = P.col[a];
+      if (v1 < v0) continue;  // arcs to lower neighbours are not level-2 edges
+      // childless edges, unless their f2 = 0 children (not stored) are summed below
+      if (ce <= cb && P.rp[v0 + 1] - (int32_t)a - 1 < P.b_side_min) continue;
       if (P.gid) {
         const int g = P.gid[v0];
         if (g != cur_g) {
@@ -709,8 +721,9 @@ __global__ void __launch_bounds__(kML3Threads, 3) motif_l3_edge(MotifArgs P) {
       const uint32_t* hArow = hA >= 0 ? P.hub_bits + (int64_t)hA * P.hub_words : nullptr;
       const uint32_t* hBrow = hB >= 0 ? P.hub_bits + (int64_t)hB * P.hub_words : nullptr;
       const int j1 = (int)(a - u0);  // v1 = A[j1]
-      const int nf0 = s - j1 - 1;    // f2 = 0 children, first in the segment
-      const bool f1any = (ce - cb) > nf0;
+      const int nf0 = s - j1 - 1;    // f2 = 0 children, first in the segment when stored
+      const bool from_b = nf0 >= P.b_side_min;  // f2 = 0 children not stored (see b_side_min)
+      const bool f1any = (ce - cb) > (from_b ? 0 : nf0);  // any stored f2 = 1 child
       const int fwA = mf_words(s, 8), shA = mf_shift(fwA);
       const int fwB = mf_words(nb, 8), shB = mf_shift(fwB);
       __syncwarp();
@@ -780,7 +793,6 @@ __global__ void __launch_bounds__(kML3Threads, 3) motif_l3_edge(MotifArgs P) {
           er += ib && !ia && x > t0;
         }
       };
-      const bool from_b = nf0 >= P.b_side_min;
       if (from_b) {
         // Base region sizes of all f2 = 0 children (v2 = A[idx], j1 < idx < s)
         // in closed form instead of per child: the sums over idx of the three
@@ -822,8 +834,8 @@ __global__ void __launch_bounds__(kML3Threads, 3) motif_l3_edge(MotifArgs P) {
           }
         }
       }
-      // the children loop: f2 = 0 children (unless done above) and f2 = 1 children
-      for (int64_t next = from_b ? cb + nf0 : cb; next < ce; next += 32) {
+      // the stored children: f2 = 0 (edges not handled from B's side) and f2 = 1
+      for (int64_t next = cb; next < ce; next += 32) {
         int32_t tag0 = 0;
         int len = 0, start = 0, tag1 = 0;
         {
@@ -835,7 +847,7 @@ __global__ void __launch_bounds__(kML3Threads, 3) motif_l3_edge(MotifArgs P) {
             const int t0 = (int)(ci - cb);
             const long long I_gt2 = ni - lower_bound_dev(I, ni, v2 + 1);  // |I & (v2, inf)|
             tag0 = v2;
-            if (t0 < nf0 && PGM_IDX_OK(a2_of(u0, j1, t0) - P.a_base, P.n_arc_slots)) {
+            if (!from_b && t0 < nf0 && PGM_IDX_OK(a2_of(u0, j1, t0) - P.a_base, P.n_arc_slots)) {
               const int idx = j1 + 1 + t0;  // v2 = A[idx]
               const int64_t a2 = (int64_t)u0 + idx;
               const uint2 tr = P.tri[a2 - P.a_base];  // (|N(v2) & A|, |N(v2) & A & (v2, inf)|)
@@ -1010,7 +1022,7 @@ __global__ void __launch_bounds__(kML3Threads, 3) motif_l3_pairs(MotifArgs P) {
   if (lane == 0 && seen) atomicAdd(P.stat, seen);
 }
 
-constexpr int kQ = 0, kErr = 7, kAcc = 8, kStat = 16, kNSlots = 32;
+constexpr int kQ = 0, kErr = 7, kAcc = 8, kStat = 16, kSkip = 24, kNSlots = 32;
 
 struct MotifRun {
   Graph& g;
@@ -1055,6 +1067,8 @@ struct MotifRun {
     P.py = ws.off[4].p;
     P.pz = ws.off[5].p;
     P.carry = ctr() + kCarrySlot;
+    P.b_side_min = o.motif_b_side_min > 0 ? o.motif_b_side_min : 32;
+    P.skipped = ctr() + kSkip;
     P.narcs = g.narcs;
     P.n_arc_slots = g.h_rp[v_hi] - g.h_rp[v_lo];
     return P;
@@ -1174,9 +1188,11 @@ struct MotifRun {
       profiler().end(id, (double)E, 12.0 * (double)E);
     }
     int64_t T = 0;
+    unsigned long long skipped = 0;  // f2 = 0 children of B-side edges: counted, not stored
     PGM_TRY(read_dev(ws.off[2].p + E, &T, s));
-    if (T == 0) return PGM_OK;
-    l3_size += (double)T;
+    PGM_TRY(read_dev(ctr() + kSkip, &skipped, s));  // zeroed with the counter block by prepare()
+    if (T == 0 && skipped == 0) return PGM_OK;
+    l3_size += (double)T + (double)skipped;
     const int64_t Bud = o.level_budget;
     int32_t pa = v_lo;
     while (pa < v_hi) {
@@ -1204,8 +1220,8 @@ struct MotifRun {
       PGM_TRY(read_dev(ws.off[2].p + (g.h_rp[pb] - a_lo), &ob, s));
       const int64_t Tp = ob - base;
       chunks++;
-      if (Tp > 0) {
-        PGM_TRY(ws.vid[3].reserve((size_t)Tp));
+      if (Tp > 0 || skipped > 0) {  // a chunk without stored children may still have B-side edges
+        PGM_TRY(ws.vid[3].reserve((size_t)std::max<int64_t>(Tp, 1)));
         MotifArgs W = args(pa, pb);
         W.a_base = a_lo;
         W.off = ws.off[2].p;
