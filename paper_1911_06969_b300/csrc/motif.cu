@@ -1230,7 +1230,9 @@ struct MotifRun {
         W.n_l3 = Tp;
         W.n_arc_slots = E;
         PGM_TRY(launch_l2<mWrite>(W, "extend_write"));
-        PGM_TRY(launch_l3(W, pa, pb, (double)Tp));
+        // entries of the algorithmic-bytes rule: the chunk's level-3 embeddings,
+        // the unstored ones (known only in total) counted with the last chunk
+        PGM_TRY(launch_l3(W, pa, pb, (double)Tp + (pb == v_hi ? (double)skipped : 0.0)));
       }
       pa = pb;
     }
