@@ -95,10 +95,9 @@ struct MotifArgs {
   const int64_t* py;
   const int64_t* pz;
   unsigned long long* carry;  // wraps of the count accumulators (add_count)
-  int b_side_min;  // last level: edges with at least this many f2 = 0 children find them from B's side
-  // (their f2 = 0 children are neither stored in the level-3 list nor read:
-  // motif_l3_pairs finds their common neighbours, motif_l3_edge sums their
-  // base region sizes in closed form); the inspection adds their number here
+  int b_side_min;  // last level: edges with at least this many f2 = 0 children are counted
+  // whole by motif_l3_pairs, from B's side; none of their children is stored
+  // in the level-3 list, and the inspection adds their number here
   unsigned long long* skipped;
   // lengths for the checked index sites (PGM_DEBUG builds)
   int64_t narcs;        // col, rev, src
@@ -212,7 +211,7 @@ __device__ __forceinline__ void l2_batch(const MotifArgs& P, const int32_t* A, i
         const uint32_t rq = wcnt[q];
         const bool fbq = s - jq - 1 >= P.b_side_min;  // this edge's f2 = 0 block is not stored
         const int64_t ic = oq + (fbq ? 0 : s - jq - 1) + rq + __popc(b & from_first & ((1u << lane) - 1u));
-        if (child && PGM_IDX_OK(ic, P.n_l3)) P.l3[ic] = (uint32_t)x | kA12;
+        if (child && !fbq && PGM_IDX_OK(ic, P.n_l3)) P.l3[ic] = (uint32_t)x | kA12;
         if (tri && !fbq && PGM_IDX_OK(oq + (xi - jq - 1), P.n_l3))
           P.l3[oq + (xi - jq - 1)] = (uint32_t)x | kA02 | kA12;
       }
@@ -312,12 +311,13 @@ __device__ __forceinline__ void l2_count_batch(const MotifArgs& P, const int32_t
     }
   }
   if (MODE == mCount) {
-    const bool fb = valid && s - j - 1 >= P.b_side_min;  // f2 = 0 children not stored
+    const bool fb = valid && s - j - 1 >= P.b_side_min;  // children not stored (see b_side_min)
+    const uint32_t nch = valid ? (uint32_t)(s - j - 1) + (uint32_t)nbj - wcnt[lane] : 0u;
     if (valid && PGM_IDX_OK(arc0 + j, P.n_arc_slots)) {
-      P.cnt[arc0 + j] = (fb ? 0u : (uint32_t)(s - j - 1)) + (uint32_t)nbj - wcnt[lane];
+      P.cnt[arc0 + j] = fb ? 0u : nch;
       P.tri[arc0 + j] = make_uint2(wcnt[lane], wcnt[32 + lane]);
     }
-    const unsigned long long sk = warp_sum((unsigned long long)(fb ? s - j - 1 : 0));
+    const unsigned long long sk = warp_sum((unsigned long long)(fb ? nch : 0u));
     if (lane == 0 && sk) atomicAdd(P.skipped, sk);
     __syncwarp();
   }
@@ -654,6 +654,79 @@ __device__ __forceinline__ void flat_scan(const int32_t* __restrict__ col, int64
 constexpr int kML3Threads = 256;  // block size of the last level (at most)
 constexpr int kML3Cap = 256;      // staging capacity (ints per list per warp) of the last level
 
+// I = A & B, sorted, into I: one warp scans the shorter list and tests its
+// elements in the other; returns |I|.
+__device__ __forceinline__ int build_I(const MotifArgs& P, const int32_t* A, int s, int hA, const int32_t* B, int nb,
+                                       int hB, int32_t* I, int64_t icap, int lane) {
+  const unsigned lt = (1u << lane) - 1u;
+  const bool iterA = s <= nb;
+  const int32_t* X = iterA ? A : B;
+  const int32_t* Y = iterA ? B : A;
+  const int nx = iterA ? s : nb, ny = iterA ? nb : s;
+  const int hy = iterA ? hB : hA;
+  int ni = 0;
+  for (int i0 = 0; i0 < nx; i0 += 32) {
+    const int i = i0 + lane;
+    bool in = false;
+    int32_t x = 0;
+    if (i < nx) {
+      x = X[i];
+      in = member(Y, ny, hy, P, x);
+    }
+    const unsigned bal = __ballot_sync(kFull, in);
+    if (in && PGM_IDX_OK(ni + __popc(bal & lt), icap)) I[ni + __popc(bal & lt)] = x;
+    ni += __popc(bal);
+  }
+  __syncwarp();
+  return ni;
+}
+
+// Base region sizes of all f2 = 0 children (v2 = A[idx], j1 < idx < s) of a
+// level-2 edge, in closed form: the sums over idx of the three sizes (A only
+// above v2; B only + v2 only; A & B + A & v2) come from the prefix arrays
+// (tri.y, |N(v2) above v0| - tri.x) and from I (the sum of |I & (v2, inf)|
+// is, over w in I above v1, the number of children below w); the a12 = 1
+// children (v2 in I above v1) are taken out of the a12 = 0 sums and added
+// with their own folding.
+__device__ __forceinline__ void f20_closed_form(const MotifArgs& P, const int32_t* A, int s, int32_t u0, int j1,
+                                                int32_t v1, int nb, const int32_t* I, int ni, int lane,
+                                                long long (&c)[6]) {
+  const int nf0 = s - j1 - 1;
+  long long sI = 0, t1 = 0, t24 = 0, t35 = 0;
+  for (int k0 = 0; k0 < ni; k0 += 32) {
+    const int k = k0 + lane;
+    if (k < ni) {
+      const int32_t w = I[k];
+      if (w > v1) {
+        const int ra = lower_bound_dev(A, s, w);  // w = A[ra]
+        sI += ra - j1 - 1;
+        const int64_t a2 = (int64_t)u0 + ra;
+        if (PGM_IDX_OK(a2 - P.a_base, P.n_arc_slots)) {
+          const uint2 tr = P.tri[a2 - P.a_base];
+          const int sl = P.rp[w + 1] - (P.rev[a2] + 1);
+          const long long igt = ni - k - 1;  // |I & (w, inf)|
+          t1 += (long long)(s - ra - 1) - igt - (long long)tr.y;
+          t24 += (long long)(nb - ni) + sl - (long long)tr.x;
+          t35 += igt + (long long)tr.y;
+        }
+      }
+    }
+  }
+  c[0] += -sI - t1;
+  c[1] += -t24;
+  c[2] += sI - t35 + t1 + t24;
+  c[4] += t35;
+  if (lane == 0) {
+    const int64_t lo = (int64_t)u0 + j1 + 1 - P.a_base, hi = (int64_t)u0 + s - P.a_base;
+    if (PGM_IDX_OK(hi, P.n_arc_slots + 1)) {
+      const long long sy = P.py[hi] - P.py[lo], sz = P.pz[hi] - P.pz[lo];
+      c[0] += (long long)nf0 * (nf0 - 1) / 2 - sy;
+      c[1] += (long long)nf0 * (nb - ni) + sz;
+      c[2] += sy;
+    }
+  }
+}
+
 __global__ void __launch_bounds__(kML3Threads, 3) motif_l3_edge(MotifArgs P) {
   extern __shared__ __align__(16) int32_t smem[];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -686,8 +759,9 @@ __global__ void __launch_bounds__(kML3Threads, 3) motif_l3_edge(MotifArgs P) {
       const int64_t ce = P.off[rel + 1] - P.off_shift;
       const int32_t v0 = P.src[a], v1 = P.col[a];
       if (v1 < v0) continue;  // arcs to lower neighbours are not level-2 edges
-      // childless edges, unless their f2 = 0 children (not stored) are summed below
-      if (ce <= cb && P.rp[v0 + 1] - (int32_t)a - 1 < P.b_side_min) continue;
+      // edges with at least b_side_min f2 = 0 children are motif_l3_pairs' (none
+      // of their children is stored); childless edges
+      if (P.rp[v0 + 1] - (int32_t)a - 1 >= P.b_side_min || ce <= cb) continue;
       if (P.gid) {
         const int g = P.gid[v0];
         if (g != cur_g) {
@@ -721,38 +795,15 @@ __global__ void __launch_bounds__(kML3Threads, 3) motif_l3_edge(MotifArgs P) {
       const uint32_t* hArow = hA >= 0 ? P.hub_bits + (int64_t)hA * P.hub_words : nullptr;
       const uint32_t* hBrow = hB >= 0 ? P.hub_bits + (int64_t)hB * P.hub_words : nullptr;
       const int j1 = (int)(a - u0);  // v1 = A[j1]
-      const int nf0 = s - j1 - 1;    // f2 = 0 children, first in the segment when stored
-      const bool from_b = nf0 >= P.b_side_min;  // f2 = 0 children not stored (see b_side_min)
-      const bool f1any = (ce - cb) > (from_b ? 0 : nf0);  // any stored f2 = 1 child
+      const int nf0 = s - j1 - 1;    // f2 = 0 children, first in the segment
       const int fwA = mf_words(s, 8), shA = mf_shift(fwA);
       const int fwB = mf_words(nb, 8), shB = mf_shift(fwB);
       __syncwarp();
       if (!hArow && restage) mf_build(FA, fwA, shA, A, s, lane);
-      if (!hBrow && (f1any || nf0 < P.b_side_min)) mf_build(FB, fwB, shB, B, nb, lane);
-      // I = A & B, sorted: scan the shorter list, test membership in the other
+      if (!hBrow) mf_build(FB, fwB, shB, B, nb, lane);
+      // I = A & B, sorted
       int32_t* I = min(s, nb) <= P.cap ? Ismem : Iglob;
-      int ni = 0;
-      {
-        const bool iterA = s <= nb;
-        const int32_t* X = iterA ? A : B;
-        const int32_t* Y = iterA ? B : A;
-        const int nx = iterA ? s : nb, ny = iterA ? nb : s;
-        const int hy = iterA ? hB : hA;
-        for (int i0 = 0; i0 < nx; i0 += 32) {
-          const int i = i0 + lane;
-          bool in = false;
-          int32_t x = 0;
-          if (i < nx) {
-            x = X[i];
-            in = member(Y, ny, hy, P, x);
-          }
-          const unsigned bal = __ballot_sync(kFull, in);
-          if (in && PGM_IDX_OK(ni + __popc(bal & lt), I == Ismem ? P.cap : P.scratch_stride))
-            I[ni + __popc(bal & lt)] = x;
-          ni += __popc(bal);
-        }
-      }
-      __syncwarp();
+      const int ni = build_I(P, A, s, hA, B, nb, hB, I, I == Ismem ? P.cap : P.scratch_stride, lane);
       if (lane == 0) seen += (unsigned long long)(nb + s);
       // region moves found by the scans (per lane): f2 = 0 children with a12
       // = 0 / 1: common neighbour in A & B above v2 (y1*), in B \ A (y2*);
@@ -793,48 +844,7 @@ __global__ void __launch_bounds__(kML3Threads, 3) motif_l3_edge(MotifArgs P) {
           er += ib && !ia && x > t0;
         }
       };
-      if (from_b) {
-        // Base region sizes of all f2 = 0 children (v2 = A[idx], j1 < idx < s)
-        // in closed form instead of per child: the sums over idx of the three
-        // sizes below come from the prefix arrays (tri.y, |N(v2) above v0| -
-        // tri.x) and from I (sum of |I & (v2, inf)| = sum over w in I above v1
-        // of the children below w); the a12 = 1 children (v2 in I, above v1)
-        // are taken out of the a12 = 0 sums and added with their own folding.
-        long long sI = 0, t1 = 0, t24 = 0, t35 = 0;
-        for (int k0 = 0; k0 < ni; k0 += 32) {
-          const int k = k0 + lane;
-          if (k < ni) {
-            const int32_t w = I[k];
-            if (w > v1) {
-              const int ra = lower_bound_dev(A, s, w);  // w = A[ra]
-              sI += ra - j1 - 1;
-              const int64_t a2 = (int64_t)u0 + ra;
-              if (PGM_IDX_OK(a2 - P.a_base, P.n_arc_slots)) {
-                const uint2 tr = P.tri[a2 - P.a_base];
-                const int sl = P.rp[w + 1] - (P.rev[a2] + 1);
-                const long long igt = ni - k - 1;  // |I & (w, inf)|
-                t1 += (long long)(s - ra - 1) - igt - (long long)tr.y;
-                t24 += (long long)(nb - ni) + sl - (long long)tr.x;
-                t35 += igt + (long long)tr.y;
-              }
-            }
-          }
-        }
-        c[0] += -sI - t1;
-        c[1] += -t24;
-        c[2] += sI - t35 + t1 + t24;
-        c[4] += t35;
-        if (lane == 0) {
-          const int64_t lo = (int64_t)u0 + j1 + 1 - P.a_base, hi = (int64_t)u0 + s - P.a_base;
-          if (PGM_IDX_OK(hi, P.n_arc_slots + 1)) {
-            const long long sy = P.py[hi] - P.py[lo], sz = P.pz[hi] - P.pz[lo];
-            c[0] += (long long)nf0 * (nf0 - 1) / 2 - sy;
-            c[1] += (long long)nf0 * (nb - ni) + sz;
-            c[2] += sy;
-          }
-        }
-      }
-      // the stored children: f2 = 0 (edges not handled from B's side) and f2 = 1
+      // the children, 32 at a time
       for (int64_t next = cb; next < ce; next += 32) {
         int32_t tag0 = 0;
         int len = 0, start = 0, tag1 = 0;
@@ -847,7 +857,7 @@ __global__ void __launch_bounds__(kML3Threads, 3) motif_l3_edge(MotifArgs P) {
             const int t0 = (int)(ci - cb);
             const long long I_gt2 = ni - lower_bound_dev(I, ni, v2 + 1);  // |I & (v2, inf)|
             tag0 = v2;
-            if (!from_b && t0 < nf0 && PGM_IDX_OK(a2_of(u0, j1, t0) - P.a_base, P.n_arc_slots)) {
+            if (t0 < nf0 && PGM_IDX_OK(a2_of(u0, j1, t0) - P.a_base, P.n_arc_slots)) {
               const int idx = j1 + 1 + t0;  // v2 = A[idx]
               const int64_t a2 = (int64_t)u0 + idx;
               const uint2 tr = P.tri[a2 - P.a_base];  // (|N(v2) & A|, |N(v2) & A & (v2, inf)|)
@@ -865,10 +875,8 @@ __global__ void __launch_bounds__(kML3Threads, 3) motif_l3_edge(MotifArgs P) {
                 c[1] += x24;
                 c[2] += x35;
               }
-              if (!from_b) {
-                start = st;
-                len = sl;
-              }
+              start = st;
+              len = sl;
               tag1 = 1 | (a12 << 1);
             } else {
               const int32_t a0 = P.rp[v2];
@@ -904,23 +912,34 @@ __global__ void __launch_bounds__(kML3Threads, 3) motif_l3_edge(MotifArgs P) {
   if (lane == 0 && seen) atomicAdd(P.stat, seen);
 }
 
-// The common neighbours of v1 and v2 above v0 for the f2 = 0 children of
-// the level-2 edges (v0, v1) that have at least b_side_min of them, found from
-// B's side: every w in B = N(v1) & (v0, inf) is extended by N(w) above v1
-// (below w when w is in A), and each element v2 in A makes the pair (v2, w):
-// w in A & B above v2, or w in B \ A, for the child (v0, v1, v2) with a12 =
-// (v2 in B).  The level-3 list itself is not read: the f2 = 0 children of
-// the edge are A above v1.  Region moves are folded into the six pattern
-// counters exactly as motif_l3_edge folds its own.
+// The level-2 edges (v0, v1) with at least b_side_min f2 = 0 children,
+// whole: none of their children is stored in the level-3 list.  Every w in
+// B = N(v1) & (v0, inf) is extended by its own list:
+//   w in A (an f2 = 0 child or below v1): N(w) in (v1, w); each element v2
+//     in A is an f2 = 0 child with the common neighbour w of v1 and v2 in
+//     A & B above v2 (y1*, a12 = v2 in B);
+//   w in B \ A (an f2 = 1 child): N(w) above v0; an element v2 in A above v1
+//     is an f2 = 0 child with the common neighbour w in B \ A (y2*), and any
+//     element x in A or B (x != v1) is an f2 = 1 region move of the child w
+//     (eh; er when x is in B \ A above w).
+// Base region sizes: the f2 = 0 children in closed form (f20_closed_form);
+// the f2 = 1 children's "B only above v2" regions sum to C(|B \ A|, 2) and
+// their "v2 only" regions to the lengths of the lists above v0 less v1.
+// All moves are folded into the six pattern counters as motif_l3_edge folds
+// its own.
 __global__ void __launch_bounds__(kML3Threads, 3) motif_l3_pairs(MotifArgs P) {
   extern __shared__ __align__(16) int32_t smem[];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   int32_t* wbase = smem + (int64_t)wid * ml3_warp_ints(P.cap);
   unsigned long long* Qe = reinterpret_cast<unsigned long long*>(wbase);
   int32_t* Qs = wbase + 128;
   uint32_t* FA = reinterpret_cast<uint32_t*>(Qs + 32);
+  uint32_t* FB = FA + kMFilterW;
   int32_t* Abuf = reinterpret_cast<int32_t*>(FA + 2 * kMFilterW);
   int32_t* Bbuf = Abuf + P.cap;
+  int32_t* Ismem = Bbuf + P.cap;
+  int32_t* Iglob = P.scratch + gw * P.scratch_stride;
   long long c[6] = {0, 0, 0, 0, 0, 0};
   unsigned long long seen = 0;
   int cur_g = -1;
@@ -938,8 +957,9 @@ __global__ void __launch_bounds__(kML3Threads, 3) motif_l3_pairs(MotifArgs P) {
       if (v1 < v0) continue;  // arcs to lower neighbours are not level-2 edges
       const int32_t u0 = P.up[v0];
       const int s = P.rp[v0 + 1] - u0;
-      const int nf0 = s - (int)(a - u0) - 1;
-      if (nf0 < P.b_side_min) continue;  // motif_l3_edge scans these children itself
+      const int j1 = (int)(a - u0);  // v1 = A[j1]
+      const int nf0 = s - j1 - 1;
+      if (nf0 < P.b_side_min) continue;  // motif_l3_edge counts these edges from the level-3 list
       if (P.gid) {
         const int g = P.gid[v0];
         if (g != cur_g) {
@@ -973,45 +993,73 @@ __global__ void __launch_bounds__(kML3Threads, 3) motif_l3_pairs(MotifArgs P) {
       } else {
         B = P.col + r0 + bstart;
       }
+      const int fwB = mf_words(nb, 8), shB = mf_shift(fwB);
       __syncwarp();
-      int y1a = 0, y1b = 0, y2a = 0, y2b = 0;
-      auto test = [&](int32_t v2, int) -> int {
-        if (hArow) return row_bit(hArow, v2) ? 3 : 0;  // exact: v2 is in A
-        return mf_test(FA, shA, v2) ? 1 : 0;
+      if (!hBrow) mf_build(FB, fwB, shB, B, nb, lane);
+      int32_t* I = min(s, nb) <= P.cap ? Ismem : Iglob;
+      const int ni = build_I(P, A, s, hA, B, nb, hB, I, I == Ismem ? P.cap : P.scratch_stride, lane);
+      f20_closed_form(P, A, s, u0, j1, v1, nb, I, ni, lane, c);
+      if (lane == 0) c[0] += (long long)(nb - ni) * (nb - ni - 1) / 2;  // B only above v2, f2 = 1 children
+      int y1a = 0, y1b = 0, y2a = 0, y2b = 0, eh = 0, er = 0;
+      // candidates: from w in A, elements in A; from w in B \ A, elements in A
+      // or B other than v1.  Knowledge bits: A known, in A, B known, in B.
+      auto test = [&](int32_t x, int w_in_A) -> int {
+        const bool ka = hArow != nullptr, kb = hBrow != nullptr;
+        const bool xa = ka && row_bit(hArow, x), xb = kb && row_bit(hBrow, x);
+        const bool ca = ka ? xa : mf_test(FA, shA, x);
+        const bool cand = w_in_A ? ca : (x != v1) & (ca | (kb ? xb : mf_test(FB, shB, x)));
+        return cand ? (1 | (ka << 1) | (xa << 2) | (kb << 3) | (xb << 4)) : 0;
       };
-      auto hit = [&](unsigned long long e, bool ok, int, int w_in_A) {
+      auto hit = [&](unsigned long long e, bool ok, int w, int w_in_A) {
         if (!ok) return;
-        const int32_t v2 = (int32_t)(uint32_t)e;
-        const bool ia = ((e >> 37) & 1) || member(A, s, -1, P, v2);
-        if (!ia) return;
-        const bool a12 = hBrow ? row_bit(hBrow, v2) : member(B, nb, -1, P, v2);
-        if (w_in_A) {
+        const int32_t x = (int32_t)(uint32_t)e;
+        const unsigned k = (unsigned)(e >> 37);
+        const bool ia = (k & 1) ? ((k >> 1) & 1) != 0 : member(A, s, -1, P, x);
+        if (w_in_A) {  // x in N(w) & (v1, w): an f2 = 0 child with the common neighbour w in A & B
+          if (!ia) return;
+          const bool a12 = (k & 4) ? ((k >> 3) & 1) != 0 : member(B, nb, -1, P, x);
           y1a += !a12;
           y1b += a12;
-        } else {
-          y2a += !a12;
-          y2b += a12;
+          return;
+        }
+        const bool ib = (k & 4) ? ((k >> 3) & 1) != 0 : member(B, nb, -1, P, x);
+        if (!ia && !ib) return;
+        eh += 1;                   // the f2 = 1 child w: x in A or B
+        er += ib && !ia && x > w;  // ... in B \ A above w
+        if (ia && x > v1) {        // the f2 = 0 child x with the common neighbour w in B \ A
+          y2a += !ib;
+          y2b += ib;
         }
       };
+      long long vonly = 0;  // f2 = 1 children: |N(w) above v0| - 1 (v1), the "v2 only" regions
       for (int w0 = 0; w0 < nb; w0 += 32) {
         int len = 0, start = 0, w_in_A = 0;
         int32_t w = 0;
         if (w0 + lane < nb) {
           w = B[w0 + lane];
           w_in_A = hArow ? row_bit(hArow, w) : member(A, s, -1, P, w);
-          // N(w) above v1 starts after the reverse arc (w, v1) of arc (v1, w); below
-          // w it ends at up[w], the first neighbour of w above w
-          const int64_t ab = (int64_t)r0 + bstart + w0 + lane;  // arc (v1, w)
-          start = PGM_IDX_OK(ab, P.narcs) ? P.rev[ab] + 1 : 0;
-          len = max((w_in_A ? P.up[w] : P.rp[w + 1]) - start, 0);
+          if (w_in_A) {
+            // N(w) in (v1, w): after the reverse arc (w, v1) of arc (v1, w), up to up[w]
+            const int64_t ab = (int64_t)r0 + bstart + w0 + lane;  // arc (v1, w)
+            start = PGM_IDX_OK(ab, P.narcs) ? P.rev[ab] + 1 : 0;
+            len = max(P.up[w] - start, 0);
+          } else {
+            // N(w) above v0
+            const int32_t wa = P.rp[w];
+            const int dw = P.rp[w + 1] - wa;
+            start = wa + lower_bound_dev(P.col + wa, dw, v0 + 1);
+            len = wa + dw - start;
+            vonly += len - 1;
+          }
         }
         seen += (unsigned long long)len;
         flat_scan<4>(P.col, P.narcs, len, start, w, w_in_A, Qe, Qs, lane, test, hit);
       }
-      // region moves (see motif_l3_edge): y1 = A & B & v2, y2 = B & v2 (not A)
-      c[0] += y1a;
-      c[1] -= 2LL * y2a;
-      c[2] += y1b - 2LL * (y1a + y2b);
+      // region moves (see motif_l3_edge): y1 = A & B & v2, y2 = B & v2 (not A);
+      // f2 = 1: eh (A or B & v2), er (B & v2 above v2)
+      c[0] += y1a - er;
+      c[1] += vonly - 2LL * y2a - eh;
+      c[2] += y1b - 2LL * (y1a + y2b) + er;
       c[3] += y2a;
       c[4] += y1a + y2b - 2LL * y1b;
       c[5] += y1b;
