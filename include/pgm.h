@@ -94,9 +94,11 @@ typedef struct {
                                     subtracted again on readback, so a count below 2^x is returned
                                     unchanged and a count of 2^x or more fails with PGM_EOVERFLOW    */
   int32_t motif_b_side_min;      /* 4-motif last level: a level-2 edge (v0, v1) with at least this many
-                                    children adjacent to v0 finds their common neighbours with v1 by
-                                    extending the members of N(v1) (one scan per edge), fewer scan each
-                                    child's own list (default 32; 1 = always, 2^30 = never)          */
+                                    children adjacent to v0 is counted whole by extending the members
+                                    of N(v1) above v0 (one scan of each member's list; none of its
+                                    children is stored in the level-3 list); an edge with fewer stores
+                                    its children and scans their lists (default 8; 1 = always, 2^30 =
+                                    never)                                                          */
   int32_t fsm_domain_order;      /* pgm_fsm, domain passes of 2-edge patterns (every call sets this field):
                                     0 = auto (by centre vertex in label order when at least half the
                                     arcs are frequent and the pass's bitmaps exceed half of L2, else by

@@ -29,7 +29,7 @@ const char* get_error() { return t_err.c_str(); }
 static std::atomic<uint64_t> g_launches{0};
 void note_launches(uint64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
-static pgm_options g_opts = {256, 512, 0, 0, (int64_t)1 << 31, 0, 2, 0, 4, 1024, 0, 0, 32, 0};
+static pgm_options g_opts = {256, 512, 0, 0, (int64_t)1 << 31, 0, 2, 0, 4, 1024, 0, 0, 8, 0};
 
 pgm_options& options() { return g_opts; }
 

@@ -574,7 +574,7 @@ pgm_status pgm_batch_autotune_ex(pgm_batch* b, int32_t k, const char* cache_path
   memset(&cur, 0, sizeof(cur));
   cur.block_threads = 256;
   cur.warp_stage_cap = 512;
-  cur.motif_b_side_min = 32;
+  cur.motif_b_side_min = 8;
   double bms = 1e30;
   bool have_ref = false;
   int nt = 0;

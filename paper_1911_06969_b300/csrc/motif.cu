@@ -1115,7 +1115,7 @@ struct MotifRun {
     P.py = ws.off[4].p;
     P.pz = ws.off[5].p;
     P.carry = ctr() + kCarrySlot;
-    P.b_side_min = o.motif_b_side_min > 0 ? o.motif_b_side_min : 32;
+    P.b_side_min = o.motif_b_side_min > 0 ? o.motif_b_side_min : 8;
     P.skipped = ctr() + kSkip;
     P.narcs = g.narcs;
     P.n_arc_slots = g.h_rp[v_hi] - g.h_rp[v_lo];
@@ -1169,7 +1169,7 @@ struct MotifRun {
     P.hub_words = g.hub_words;
     const int threads = std::min(o.block_threads, kML3Threads);
     P.cap = std::min(cap, kML3Cap);
-    P.b_side_min = o.motif_b_side_min > 0 ? o.motif_b_side_min : 32;
+    P.b_side_min = o.motif_b_side_min > 0 ? o.motif_b_side_min : 8;
     // (threads / 32) warps of at most 5.8 KB: four blocks fit an SM
     const size_t wsmem = (size_t)(threads / 32) * ml3_warp_ints(P.cap) * sizeof(int32_t);
     PGM_TRY(smem_attr((const void*)motif_l3_edge, (int)std::max<size_t>(wsmem, 200 * 1024)));
