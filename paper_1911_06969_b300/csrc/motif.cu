@@ -730,7 +730,6 @@ __device__ __forceinline__ void f20_closed_form(const MotifArgs& P, const int32_
 __global__ void __launch_bounds__(kML3Threads, 3) motif_l3_edge(MotifArgs P) {
   extern __shared__ __align__(16) int32_t smem[];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const unsigned lt = (1u << lane) - 1u;
   const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   int32_t* wbase = smem + (int64_t)wid * ml3_warp_ints(P.cap);
   unsigned long long* Qe = reinterpret_cast<unsigned long long*>(wbase);  // candidate queue
