@@ -139,6 +139,25 @@ def test_motif_orders(order):
         pgm.pgm_set_options(motif_order=0)
 
 
+@pytest.mark.parametrize("bmin", [1, 2, 8, 33, 1 << 30])
+def test_motif_b_side_threshold(bmin):
+    """4-motif counts equal the oracle's whichever level-2 edges the B-side
+    kernel counts whole (f2 = 0 children >= bmin: nothing stored, closed-form
+    base regions, f2 = 1 children from the scans of N(w)) and which the
+    level-3 list keeps (1 = every edge from B's side, 2^30 = none), on both
+    vertex orders, with hubs (bitmaps) and without, and across edge-blocking
+    chunks (small level budget)."""
+    try:
+        for order in (0, 1):
+            pgm.pgm_set_options(motif_b_side_min=bmin, motif_order=order, level_budget=4096)
+            for g in [gg.barabasi_albert(2500, 9, seed=31), gg.erdos_renyi(300, 0.2, seed=32),
+                      gg.chung_lu(3000, 2.1, 12.0, 600.0, 33), gg.complete(45), gg.star(70),
+                      gg.complete_multipartite((12, 20, 25)), gg.cycle(50)]:
+                assert gpu_motifs(g, 4) == oracle.formula_motifs(g, 4), (g.name, bmin, order)
+    finally:
+        pgm.pgm_set_options(motif_b_side_min=8, motif_order=0, level_budget=1 << 31)
+
+
 def test_small_tiles_hub_paths(small_tiles):
     for g in [gg.barabasi_albert(2000, 12, seed=8), gg.complete(80), gg.rmat(1 << 12, 30000, seed=9),
               gg.complete_multipartite((30, 30, 30))]:
