@@ -795,8 +795,8 @@ __global__ void __launch_bounds__(kML3Threads, 3) motif_l3_edge(MotifArgs P) {
       const uint32_t* hBrow = hB >= 0 ? P.hub_bits + (int64_t)hB * P.hub_words : nullptr;
       const int j1 = (int)(a - u0);  // v1 = A[j1]
       const int nf0 = s - j1 - 1;    // f2 = 0 children, first in the segment
-      const int fwA = mf_words(s, 8), shA = mf_shift(fwA);
-      const int fwB = mf_words(nb, 8), shB = mf_shift(fwB);
+      const int fwA = mf_words(s, 16), shA = mf_shift(fwA);
+      const int fwB = mf_words(nb, 16), shB = mf_shift(fwB);
       __syncwarp();
       if (!hArow && restage) mf_build(FA, fwA, shA, A, s, lane);
       if (!hBrow) mf_build(FB, fwB, shB, B, nb, lane);
@@ -979,7 +979,7 @@ __global__ void __launch_bounds__(kML3Threads, 3) motif_l3_pairs(MotifArgs P) {
       } else {
         A = P.col + u0;
       }
-      const int fwA = mf_words(s, 8), shA = mf_shift(fwA);
+      const int fwA = mf_words(s, 16), shA = mf_shift(fwA);
       __syncwarp();
       if (!hArow && restage) mf_build(FA, fwA, shA, A, s, lane);
       const int32_t r0 = P.rp[v1], r1 = P.rp[v1 + 1];
@@ -992,7 +992,7 @@ __global__ void __launch_bounds__(kML3Threads, 3) motif_l3_pairs(MotifArgs P) {
       } else {
         B = P.col + r0 + bstart;
       }
-      const int fwB = mf_words(nb, 8), shB = mf_shift(fwB);
+      const int fwB = mf_words(nb, 16), shB = mf_shift(fwB);
       __syncwarp();
       if (!hBrow) mf_build(FB, fwB, shB, B, nb, lane);
       int32_t* I = min(s, nb) <= P.cap ? Ismem : Iglob;
