@@ -251,7 +251,7 @@ def main(argv=None):
                     help="profiling: time only motif counting (--motif-k) on a graph of N vertices")
     ap.add_argument("--motif-k", type=int, default=4, choices=[3, 4, 5],
                     help="profiling: motif size of --motif-only (3, 4: Chung-Lu graph; 5: G(N, 10/(N-1)))")
-    ap.add_argument("--fsm-only", default="", choices=["", "mico_like", "patent_like"],
+    ap.add_argument("--fsm-only", default="", choices=["", "mico_like", "patent_like", "youtube_like"],
                     help="profiling: time only frequent subgraph mining on this labelled stand-in")
     ap.add_argument("--fsm-edges", type=int, default=2, help="profiling: pattern edges of --fsm-only (3-FSM = 2)")
     ap.add_argument("--fsm-support", type=int, default=300, help="profiling: min_support of --fsm-only")
@@ -625,7 +625,8 @@ def fsm_only(args):
 
     from paper_1911_06969_b300 import pgm
 
-    make, nlab = {"mico_like": (gg.mico_like, 29), "patent_like": (gg.patent_like, 37)}[args.fsm_only]
+    make, nlab = {"mico_like": (gg.mico_like, 29), "patent_like": (gg.patent_like, 37),
+                  "youtube_like": (gg.youtube_like, 29)}[args.fsm_only]
     g = make()
     with pgm.Graph(g) as G:
         G.set_labels(gg.vertex_labels(g.n, nlab, seed=1, skew=1.0))
@@ -651,13 +652,15 @@ def fsm_shape_totals(g):
 
 
 def fsm(pgm, torch):
-    """Frequent subgraph mining on the Mico and Patents stand-ins (29 / 37
-    skewed labels): 3-FSM (patterns of up to 2 edges) at the paper's
-    min_support values 300, 500, 1000, 5000, and 4-FSM (up to 3 edges) on
-    the Patents stand-in at 30K, 20K, 15K.  Wall time of the whole call
-    (host result assembly included; the call synchronises)."""
+    """Frequent subgraph mining on the Mico, Patents and Youtube stand-ins
+    (29 / 37 / 29 skewed labels): 3-FSM (patterns of up to 2 edges) at the
+    paper's min_support values 300, 500, 1000, 5000 (300 and 5000 on
+    Youtube), and 4-FSM (up to 3 edges) on the Patents stand-in at 30K, 20K,
+    15K.  Wall time of the whole call (host result assembly included; the
+    call synchronises)."""
     out = {}
-    for name, make, nlab in (("mico_like", gg.mico_like, 29), ("patent_like", gg.patent_like, 37)):
+    for name, make, nlab in (("mico_like", gg.mico_like, 29), ("patent_like", gg.patent_like, 37),
+                             ("youtube_like", gg.youtube_like, 29)):
         g = make()
         lab = gg.vertex_labels(g.n, nlab, seed=1, skew=1.0)
         rows = {}
@@ -667,7 +670,7 @@ def fsm(pgm, torch):
             sums = {"1": 0, "2": 0}
             for p in full:
                 sums[str(p["edges"])] += p["embeddings"]
-            runs = [(2, s) for s in (300, 500, 1000, 5000)]
+            runs = [(2, s) for s in ((300, 5000) if name == "youtube_like" else (300, 500, 1000, 5000))]
             if name == "patent_like":
                 runs += [(3, s) for s in (30000, 20000, 15000)]
             for me, sigma in runs:

@@ -340,6 +340,14 @@ def mico_like(seed: int = 1) -> CSR:
     return _cached(f"micolike_s{seed}", lambda: chung_lu(100_000, 2.1, 21.6, 1359.0, seed))
 
 
+def youtube_like(seed: int = 1) -> CSR:
+    """Stand-in for the paper's Youtube input (Table 1: 7,066,392 vertices,
+    114,190,484 arcs, average degree 16, 29 labels): Chung-Lu, n =
+    7,066,392, exponent 2.2, mean weight 16.2, weights capped at 2,000; its
+    labels are vertex_labels(n, 29, seed, skew=1.0)."""
+    return _cached(f"youtubelike_s{seed}", lambda: chung_lu(7_066_392, 2.2, 16.2, 2000.0, seed))
+
+
 def patent_like(seed: int = 1) -> CSR:
     """Stand-in for the paper's Patents input (Table 1: 2,745,761 vertices,
     27,930,818 arcs, average degree 10, 37 labels): Chung-Lu, n = 2,745,761,
