@@ -208,8 +208,34 @@ pgm_status read_counters(const unsigned long long* dev, unsigned long long* host
     *deferred = true;
     return PGM_OK;
   }
-  PGM_TRY_CUDA(cudaMemcpyAsync(host, dev, n * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+  // through a page-locked staging buffer of this thread: a copy to pageable
+  // memory takes the driver's own staging path, which costs several
+  // microseconds per call on the small counts where launch latency is the
+  // whole run time
+  struct Staging {
+    unsigned long long* p = nullptr;
+    size_t n = 0;
+    ~Staging() {
+      if (p) cudaFreeHost(p);
+    }
+  };
+  static thread_local Staging st;
+  if (st.n < n) {
+    if (st.p) cudaFreeHost(st.p);
+    st.p = nullptr;
+    st.n = 0;
+    const size_t want = std::max<size_t>(n, 256);
+    if (cudaHostAlloc(&st.p, want * sizeof(unsigned long long), cudaHostAllocPortable) == cudaSuccess) {
+      st.n = want;
+    } else {
+      cudaGetLastError();
+      st.p = nullptr;
+    }
+  }
+  unsigned long long* dst = st.p ? st.p : host;
+  PGM_TRY_CUDA(cudaMemcpyAsync(dst, dev, n * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
   PGM_TRY_CUDA(cudaStreamSynchronize(s));
+  if (dst != host) memcpy(host, dst, n * sizeof(unsigned long long));
   *deferred = false;
   return PGM_OK;
 }

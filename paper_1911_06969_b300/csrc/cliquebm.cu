@@ -61,6 +61,7 @@ struct BmArgs {
   unsigned long long* deep;   // k >= 6: [t] entries of level t + 3 (t = 2 .. k - 4)
   int clevels;                // C buffers per warp: 1, or k - 4 for k >= 6
   unsigned long long* carry;  // wraps of the count accumulators (add_count)
+  int grab;                   // vertices a warp of the warp kernel takes per queue grab
 };
 
 // bucket of a vertex with out-degree d > kBmWarpD
@@ -297,10 +298,10 @@ __global__ void __launch_bounds__(256, DEEP ? 4 : 8) bm_warp_kernel(BmArgs B) {
   const int64_t np = (int64_t)B.v_hi - B.v_lo;
   for (;;) {
     unsigned long long p0 = 0;
-    if (lane == 0) p0 = atomicAdd(B.queue, (unsigned long long)kBmGrab);
+    if (lane == 0) p0 = atomicAdd(B.queue, (unsigned long long)B.grab);
     p0 = __shfl_sync(kFull, p0, 0);
     if ((int64_t)p0 >= np) break;
-    const int64_t pend = min((int64_t)p0 + kBmGrab, np);
+    const int64_t pend = min((int64_t)p0 + B.grab, np);
     for (int64_t pi = (int64_t)p0; pi < pend; pi++) {
       const int32_t u = (int32_t)(B.v_lo + pi);
       const int32_t a0 = B.rp[u];
@@ -959,7 +960,11 @@ pgm_status count_kcliques_bitset(Graph& g, Workspace& ws, cudaStream_t s, int k,
   B.deep = ws.ctr.p + kDeepLvl;
   B.clevels = clevels;
   int wgrid = grid_for(warp_fn, 256, 0);
-  wgrid = (int)std::max<int64_t>(1, std::min<int64_t>(wgrid, ((nv + kBmGrab - 1) / kBmGrab + 7) / 8));
+  // kBmGrab vertices per grab, fewer when the graph has too few vertices to
+  // give every resident warp that many (a small graph's run time is the
+  // chain of row builds of one warp's vertices)
+  B.grab = (int)std::max<int64_t>(1, std::min<int64_t>(kBmGrab, nv / ((int64_t)wgrid * 8)));
+  wgrid = (int)std::max<int64_t>(1, std::min<int64_t>(wgrid, ((nv + B.grab - 1) / B.grab + 7) / 8));
   // The buckets depend on the warp kernel (it fills their vertex lists) but
   // not on one another: outside a stream capture or a plan recording they
   // run on forked streams, so that one bucket's tail overlaps the next.
