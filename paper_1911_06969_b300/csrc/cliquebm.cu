@@ -62,6 +62,7 @@ struct BmArgs {
   int clevels;                // C buffers per warp: 1, or k - 4 for k >= 6
   unsigned long long* carry;  // wraps of the count accumulators (add_count)
   int grab;                   // vertices a warp of the warp kernel takes per queue grab
+  int classified;             // 1: bm_classify_kernel filled the bucket lists beforehand
 };
 
 // bucket of a vertex with out-degree d > kBmWarpD
@@ -308,7 +309,7 @@ __global__ void __launch_bounds__(256, DEEP ? 4 : 8) bm_warp_kernel(BmArgs B) {
       const int d = B.rp[u + 1] - a0;
       if (d < 2) continue;  // no triangle (hence no level-3 entry) rooted at u
       if (d > kBmWarpD) {
-        if (lane == 0) {
+        if (lane == 0 && !B.classified) {
           const int b = bm_bucket(d, B.smem_d);
           unsigned long long x = atomicAdd(B.queue + kQPush + b, 1ull);
           if ((int64_t)x < B.big_cap[b])
@@ -401,6 +402,24 @@ __global__ void __launch_bounds__(256, DEEP ? 4 : 8) bm_warp_kernel(BmArgs B) {
   }
   seen = warp_sum(seen);
   if (lane == 0 && seen) atomicAdd(B.stat, seen);
+}
+
+// The vertices of out-degree above kBmWarpD into their buckets' lists, one
+// thread per vertex: run before the warp kernel, it lets the bucket kernels
+// start without waiting for the warp kernel.
+__global__ void bm_classify_kernel(BmArgs B) {
+  const int64_t np = (int64_t)B.v_hi - B.v_lo;
+  for (int64_t pi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; pi < np; pi += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t u = (int32_t)(B.v_lo + pi);
+    const int d = B.rp[u + 1] - B.rp[u];
+    if (d <= kBmWarpD) continue;
+    const int b = bm_bucket(d, B.smem_d);
+    const unsigned long long x = atomicAdd(B.queue + kQPush + b, 1ull);
+    if ((int64_t)x < B.big_cap[b])
+      B.big[B.big_off[b] + (int64_t)x] = u;
+    else
+      atomicAdd(B.err, 1ull);
+  }
 }
 
 // ---------------------------------------------------------- block kernels
@@ -965,9 +984,10 @@ pgm_status count_kcliques_bitset(Graph& g, Workspace& ws, cudaStream_t s, int k,
   // chain of row builds of one warp's vertices)
   B.grab = (int)std::max<int64_t>(1, std::min<int64_t>(kBmGrab, nv / ((int64_t)wgrid * 8)));
   wgrid = (int)std::max<int64_t>(1, std::min<int64_t>(wgrid, ((nv + B.grab - 1) / B.grab + 7) / 8));
-  // The buckets depend on the warp kernel (it fills their vertex lists) but
-  // not on one another: outside a stream capture or a plan recording they
-  // run on forked streams, so that one bucket's tail overlaps the next.
+  // The buckets depend on their vertex lists (filled by the warp kernel, or
+  // beforehand by bm_classify_kernel) but not on one another: outside a
+  // stream capture or a plan recording they run on forked streams, so that
+  // one bucket's tail overlaps the next.
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   PGM_TRY_CUDA(cudaStreamIsCapturing(s, &cap));
   ForkStreams* F = nullptr;
@@ -976,9 +996,20 @@ pgm_status count_kcliques_bitset(Graph& g, Workspace& ws, cudaStream_t s, int k,
   int id = prof.begin("bitset_count", 3);
   if (nv > 0) {
     void* wargv[] = {&B};
+    // forked, with bucket vertices present: the bucket lists first (one
+    // thread per vertex), then the warp kernel on the caller's stream and
+    // the bucket kernels on the forked streams, all three at once
+    const bool pre = F && g.dag_dmax > kBmWarpD;
+    B.classified = pre ? 1 : 0;
+    if (pre) {
+      const int cgrid = (int)std::max<int64_t>(1, std::min<int64_t>((nv + 255) / 256, 8LL * num_sms()));
+      bm_classify_kernel<<<cgrid, 256, 0, s>>>(B);
+      PGM_CHECK_LAUNCH();
+      PGM_TRY_CUDA(cudaEventRecord(F->ev[0], s));
+    }
     PGM_TRY_CUDA(cudaLaunchKernel(warp_fn, dim3(wgrid), dim3(256), wargv, 0, s));
     PGM_CHECK_LAUNCH();
-    if (F) PGM_TRY_CUDA(cudaEventRecord(F->ev[0], s));
+    if (F && !pre) PGM_TRY_CUDA(cudaEventRecord(F->ev[0], s));
     // largest rows first, so that the short tail of each launch is cheap
     int nf = 0;
     for (int b = kBmBuckets - 1; b >= 0; b--) {
