@@ -197,10 +197,14 @@ struct CliqueRun {
     PGM_TRY(smem_attr(wfn, 160 * 1024));
     PGM_TRY(smem_attr(bfn, 160 * 1024));
     int wgrid = grid_for(wfn, threads, wsmem);
-    const int64_t warps_needed = (nparents + kGrab - 1) / kGrab;
+    // kGrab parents per queue access, fewer when there are too few parents
+    // to give every resident warp that many
+    A.grab = (int)std::max<int64_t>(1, std::min<int64_t>(kGrab, nparents / ((int64_t)wgrid * (threads / 32))));
+    const int64_t warps_needed = (nparents + A.grab - 1) / A.grab;
     wgrid = (int)std::max<int64_t>(1, std::min<int64_t>(wgrid, (warps_needed + threads / 32 - 1) /
                                                                     (threads / 32)));
-    int bgrid = grid_for(bfn, 512, bsmem);
+    // a block takes one hub parent at a time: no more blocks than hubs can exist
+    const int bgrid = (int)std::max<int64_t>(1, std::min<int64_t>(grid_for(bfn, 512, bsmem), big_cap));
     Profiler& prof = profiler();
     int id = prof.begin(name, level);
     if (L.seg32) {

@@ -38,6 +38,7 @@ struct LevelArgs {
   const int32_t* gid;         // vertex -> graph (batches) or nullptr
   unsigned long long* per_graph;  // kSum with gid: per-graph counts
   unsigned long long* carry;      // wraps of the count accumulators (add_count)
+  int grab;                       // parents a warp takes per queue access (<= 0: kGrab)
 };
 
 // Flush a per-lane count to the graph's counter (warp-wide reduction).
@@ -237,12 +238,13 @@ __global__ void __launch_bounds__(512) clique_warp_kernel(LevelArgs A) {
   unsigned long long tot = 0, lensum = 0;
   int cur_g = -1;
   const int64_t np = A.p_hi - A.p_lo;
+  const int grab = A.grab > 0 ? A.grab : kGrab;
   for (;;) {
     unsigned long long p0 = 0;
-    if (lane == 0) p0 = atomicAdd(A.queue, (unsigned long long)kGrab);
+    if (lane == 0) p0 = atomicAdd(A.queue, (unsigned long long)grab);
     p0 = __shfl_sync(kFull, p0, 0);
     if ((int64_t)p0 >= np) break;
-    const int64_t pend = min((int64_t)p0 + kGrab, np);
+    const int64_t pend = min((int64_t)p0 + grab, np);
     for (int64_t pi = (int64_t)p0; pi < pend; pi++) {
       const int64_t p = A.p_lo + pi;
       const int64_t sb = (int64_t)seg[p] - A.seg_shift;

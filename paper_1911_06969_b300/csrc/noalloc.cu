@@ -117,9 +117,10 @@ extern "C" pgm_status pgm_count_triangles_noalloc(int32_t n, const int32_t* dag_
     PGM_TRY(smem_attr(wfn, 160 * 1024));
     PGM_TRY(smem_attr(bfn, 160 * 1024));
     int wgrid = grid_for(wfn, threads, wsmem);
-    const int64_t warps_needed = ((int64_t)n + kGrab - 1) / kGrab;
+    A.grab = (int)std::max<int64_t>(1, std::min<int64_t>(kGrab, (int64_t)n / ((int64_t)wgrid * (threads / 32))));
+    const int64_t warps_needed = ((int64_t)n + A.grab - 1) / A.grab;
     wgrid = (int)std::max<int64_t>(1, std::min<int64_t>(wgrid, (warps_needed + threads / 32 - 1) / (threads / 32)));
-    const int bgrid = grid_for(bfn, 512, bsmem);
+    const int bgrid = (int)std::max<int64_t>(1, std::min<int64_t>(grid_for(bfn, 512, bsmem), big_need));
     clique_warp_kernel<kSum, int32_t><<<wgrid, threads, wsmem, s>>>(A);
     PGM_CHECK_LAUNCH();
     clique_block_kernel<kSum, int32_t><<<bgrid, 512, bsmem, s>>>(A);
@@ -127,10 +128,12 @@ extern "C" pgm_status pgm_count_triangles_noalloc(int32_t n, const int32_t* dag_
   }
   PGM_TRY_CUDA(cudaMemcpyAsync(count_dev, sc->ctr + kNaAcc, sizeof(unsigned long long),
                                cudaMemcpyDeviceToDevice, s));
-  unsigned long long err = 0, carry = 0;
-  PGM_TRY_CUDA(cudaMemcpyAsync(&err, sc->ctr + kNaErr, sizeof(err), cudaMemcpyDeviceToHost, s));
-  PGM_TRY_CUDA(cudaMemcpyAsync(&carry, sc->ctr + kCarrySlot, sizeof(carry), cudaMemcpyDeviceToHost, s));
+  // the carry and error slots in one readback (slots kCarrySlot .. kNaErr)
+  static_assert(kCarrySlot < kNaErr, "carry slot below the error slot");
+  unsigned long long h[kNaErr - kCarrySlot + 1];
+  PGM_TRY_CUDA(cudaMemcpyAsync(h, sc->ctr + kCarrySlot, sizeof(h), cudaMemcpyDeviceToHost, s));
   PGM_TRY_CUDA(cudaStreamSynchronize(s));
+  const unsigned long long err = h[kNaErr - kCarrySlot], carry = h[0];
   if (err) {
     set_error("pgm_count_triangles_noalloc: hub list overflow");
     return PGM_ENOMEM;
