@@ -102,6 +102,26 @@ def test_clique_engines(engine):
         pgm.pgm_set_options(clique_engine=0)
 
 
+@pytest.mark.parametrize("engine", [1, 2])
+def test_warp_grab_sizes(engine):
+    """Vertex counts that set the warp kernels' grab (parents per queue
+    access) anywhere from one to the full grab: a few thousand vertices (one
+    per grab) up to 10^5 (the full grab), with hub vertices so that the
+    bucket lists and block kernels take part too."""
+    pgm.pgm_set_options(clique_engine=engine)
+    try:
+        for g in [gg.barabasi_albert(2000, 8, seed=61), gg.rmat(20000, 160000, seed=62),
+                  gg.rmat(40000, 320000, seed=63), gg.rmat(100000, 800000, seed=64)]:
+            if g.name not in _GRAB_WANT:
+                _GRAB_WANT[g.name] = [oracle.clique_count(g, k, "degree") for k in (3, 4)]
+            assert gpu_cliques(g, [3, 4]) == _GRAB_WANT[g.name], g.name
+    finally:
+        pgm.pgm_set_options(clique_engine=0)
+
+
+_GRAB_WANT = {}  # oracle counts, shared by the two engines' runs
+
+
 @pytest.mark.parametrize("smem_degree,fwd", [(64, 1), (256, 1000), (512, 8), (1024, 1), (1024, 1000)])
 def test_bitset_buckets(smem_degree, fwd):
     """Bitset engine: every out-degree bucket (rows in shared memory up to
