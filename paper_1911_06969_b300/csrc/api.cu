@@ -70,6 +70,23 @@ int num_sms() {
   return cached[d];
 }
 
+int64_t l2_bytes() {
+  static int64_t cached[64] = {0};
+  static std::mutex mu;
+  int d = device_id();
+  if (d < 0 || d >= 64) return 0;
+  std::lock_guard<std::mutex> lk(mu);
+  if (!cached[d]) {
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrL2CacheSize, d) != cudaSuccess || v <= 0) {
+      cudaGetLastError();
+      v = 0;
+    }
+    cached[d] = v > 0 ? v : -1;
+  }
+  return cached[d] > 0 ? cached[d] : 0;
+}
+
 // occupancy is cached per (kernel, block size, shared memory) so that no
 // runtime query happens while a stream is being captured
 int grid_for(const void* fn, int threads, size_t smem) {

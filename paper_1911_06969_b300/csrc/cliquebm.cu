@@ -996,10 +996,14 @@ pgm_status count_kcliques_bitset(Graph& g, Workspace& ws, cudaStream_t s, int k,
   int id = prof.begin("bitset_count", 3);
   if (nv > 0) {
     void* wargv[] = {&B};
-    // forked, with bucket vertices present: the bucket lists first (one
-    // thread per vertex), then the warp kernel on the caller's stream and
-    // the bucket kernels on the forked streams, all three at once
-    const bool pre = F && g.dag_dmax > kBmWarpD;
+    // forked, with bucket vertices present and a DAG that fits the L2: the
+    // bucket lists first (one thread per vertex), then the warp kernel on
+    // the caller's stream and the bucket kernels on the forked streams, all
+    // at once.  (Measured: R-MAT 21, a 120 MB DAG, 20.60 -> 20.46 ms; R-MAT
+    // scale 24, 0.7 GB, 167 -> 171 ms, the warp kernel's scattered reads
+    // then sharing the L2 with the buckets' rows: there the buckets wait.)
+    const int64_t dag_bytes = 4 * ((int64_t)g.narcs / 2 + (int64_t)g.n + 1);
+    const bool pre = F && g.dag_dmax > kBmWarpD && dag_bytes <= l2_bytes();
     B.classified = pre ? 1 : 0;
     if (pre) {
       const int cgrid = (int)std::max<int64_t>(1, std::min<int64_t>((nv + 255) / 256, 8LL * num_sms()));

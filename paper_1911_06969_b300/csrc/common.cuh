@@ -75,6 +75,7 @@ unsigned long long count_seed();
 constexpr int kCarrySlot = 5;
 pgm_status seed_counts(unsigned long long* dev, int n, cudaStream_t s);
 int num_sms();            // SM count of the current device
+int64_t l2_bytes();       // L2 cache size of the current device (bytes)
 int device_id();
 
 // ----------------------------------------------------------- device memory
