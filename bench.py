@@ -44,6 +44,7 @@ sys.path.insert(0, ROOT)
 import graphgen as gg  # noqa: E402
 
 METRIC = "embeddings/s and wall time for 4-clique & 4-motif (exact); batched vs plain speedup"
+NOMINAL_HBM_GBS = 8000.0  # nominal HBM3e bandwidth of the part (GB/s); the measured copy peak is `peak`
 WORKLOAD = "4-clique count, R-MAT scale 21 (a,b,c,d)=(0.57,0.19,0.19,0.05), 28,000,000 undirected edges, degree-oriented DAG"
 GOLD = os.path.join(ROOT, "tests", "golden")
 KERNELS = {
@@ -400,6 +401,15 @@ def roofline(g, k, dom, dom_ms, dom_bytes, dom_launches, full, clk, pgm, torch):
          "traffic": traffic_rec.get(key) if full else None, "kernel": KERNELS.get(dom, dom),
          "kernel_ms_per_launch": kms, "alg_bytes_per_launch": bpl,
          "alg_bytes_rule": "sum over DAG arcs u->v of (4 d+(v) + 8) + 8 |L3| (level 2 -> 3)"}
+    # the same against the nominal HBM bandwidth, the DRAM rate that the ncu
+    # byte count implies at this launch time, and the L2 / SM figures of the
+    # device the line was measured on
+    r["peak_nominal"] = NOMINAL_HBM_GBS
+    r["frac_nominal"] = achieved / NOMINAL_HBM_GBS if achieved else None
+    if r["traffic"] and kms > 0:
+        r["dram_GBps_from_traffic"] = r["traffic"] / (kms * 1e-3) / 1e9
+    props = torch.cuda.get_device_properties(0)
+    r["device"] = {"sms": props.multi_processor_count, "l2_bytes": getattr(props, "L2_cache_size", None)}
     if full:
         s3 = level3_last_outdeg_sum(g, pgm, torch)
         if s3 is not None:
