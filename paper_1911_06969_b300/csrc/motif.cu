@@ -103,6 +103,7 @@ struct MotifArgs {
   int64_t narcs;        // col, rev, src
   int64_t n_arc_slots;  // cnt, tri (arcs of the launch's vertex range)
   int64_t n_l3;         // l3 entries of the chunk
+  int grab;             // level 2: vertices a warp takes per queue access (<= 0: kMGrab)
 };
 
 template <int N>
@@ -345,12 +346,13 @@ __global__ void __launch_bounds__(512, 2) motif_l2_warp(MotifArgs P) {
   unsigned long long seen = 0;
   int cur_g = -1;
   const int64_t np = (int64_t)P.v_hi - P.v_lo;
+  const int grab = P.grab > 0 ? P.grab : kMGrab;
   for (;;) {
     unsigned long long p0 = 0;
-    if (lane == 0) p0 = atomicAdd(P.queue, (unsigned long long)kMGrab);
+    if (lane == 0) p0 = atomicAdd(P.queue, (unsigned long long)grab);
     p0 = __shfl_sync(kFull, p0, 0);
     if ((int64_t)p0 >= np) break;
-    const int64_t pend = min((int64_t)p0 + kMGrab, np);
+    const int64_t pend = min((int64_t)p0 + grab, np);
     for (int64_t pi = (int64_t)p0; pi < pend; pi++) {
       const int32_t v0 = (int32_t)(P.v_lo + pi);
       const int32_t u0 = P.up[v0], u1 = P.rp[v0 + 1];
@@ -1137,7 +1139,10 @@ struct MotifRun {
     PGM_TRY(smem_attr((const void*)motif_l2_block<MODE>, 160 * 1024));
     const int64_t np = (int64_t)P.v_hi - P.v_lo;
     int wgrid = grid_for((const void*)motif_l2_warp<MODE>, threads, wsmem);
-    const int64_t blocks_needed = ((np + kMGrab - 1) / kMGrab + threads / 32 - 1) / (threads / 32);
+    // kMGrab vertices per queue access, one when there are fewer than that
+    // many per resident warp (small graphs: a warp's vertices run in series)
+    P.grab = (int)std::max<int64_t>(1, std::min<int64_t>(kMGrab, np / ((int64_t)wgrid * (threads / 32))));
+    const int64_t blocks_needed = ((np + P.grab - 1) / P.grab + threads / 32 - 1) / (threads / 32);
     wgrid = (int)std::max<int64_t>(1, std::min<int64_t>(wgrid, blocks_needed));
     const int bgrid = grid_for((const void*)motif_l2_block<MODE>, 512, bsmem);
     Profiler& prof = profiler();
